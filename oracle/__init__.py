@@ -1,0 +1,291 @@
+"""FP64 CPU oracle for exact brickwork-circuit amplitudes.
+
+TEST INFRASTRUCTURE ONLY. Only ``tests/``, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline / reference leg may import this package. The product
+path (the CUDA library and its binding) never imports, links or calls it, and
+this package never imports the product. The only module both sides read is the
+seeded input generator ``workloads``, which holds no arithmetic of the method.
+
+What it computes (the paper's amplitude, Sec. 2.2): psi(x) = <x|U|0^n> for an
+open 1D brickwork circuit with CZ entanglers (Sec. 2.1), in several independent
+ways:
+
+* ``sv_state`` / ``sv_amplitudes`` -- dense state vector, gate by gate (C);
+* ``nb_amplitudes`` -- naive row-by-row contraction of the circuit's tensor
+  network (Sec. 2.2 mapping; every row absorbed in forward time with an explicit
+  wire index; no snake order, slot reuse, fusion or rescaling) (C);
+* ``feynman_amplitude`` -- brute-force sum over every CZ-layer value (C);
+* ``kron_state`` -- product of full 2^n x 2^n layer matrices (numpy);
+* ``tableau_probability`` -- |psi|^2 of Clifford-only circuits from an
+  Aaronson-Gottesman stabilizer tableau (C);
+* ``closed_form_hdiag`` -- closed form for circuits whose first and last slots
+  are H on every qubit and whose interior slots are diagonal (numpy);
+* ``log_xeb`` -- the log-XEB estimator of Sec. 5.2 (numpy).
+
+Readings of points the paper leaves open (also listed in the design notes):
+d+1 one-qubit slots, slot t < d before CZ layer t; U_(q,t) = T^tau . C (the
+Clifford acts first); T = diag(1, e^(i pi/4)); the 24 Cliffords are
+C_k = P_(k mod 4) . R_(k div 4) with P in (I, X, Y, Z), Y = [[0,-i],[i,0]],
+R in (I, H, S, S.H, H.S, H.S.H); layer l couples (i, i+1) for i = l (mod 2).
+
+Pins: see tests/test_oracle_pins.py (brute force, Kronecker product, norm,
+tableau, closed form, identity circuit). Every function here is pinned.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tbo.c")
+_LIB_PATH = os.path.join(_HERE, "libtbo.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C part of the oracle (gcc, OpenMP) next to its source."""
+    if force or not os.path.exists(_LIB_PATH) or \
+            os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", _SRC,
+               "-o", _LIB_PATH + ".tmp", "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(_LIB_PATH + ".tmp", _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        dp = ctypes.POINTER(ctypes.c_double)
+        u8p = ctypes.POINTER(ctypes.c_uint8)
+        ip = ctypes.POINTER(ctypes.c_int)
+        lib.tbo_sv_state.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp]
+        lib.tbo_nb_amplitude.argtypes = [ctypes.c_int, ctypes.c_int, dp, u8p, dp, ip]
+        lib.tbo_feynman.argtypes = [ctypes.c_int, ctypes.c_int, dp, u8p, dp]
+        lib.tbo_tableau_prob.argtypes = [ctypes.c_int, ctypes.c_int, u8p, u8p, dp]
+        lib.tbo_num_threads.argtypes = []
+        for f in ("tbo_sv_state", "tbo_nb_amplitude", "tbo_feynman", "tbo_tableau_prob",
+                  "tbo_num_threads"):
+            getattr(lib, f).restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def num_threads() -> int:
+    """OpenMP threads the C oracle uses."""
+    return int(_load().tbo_num_threads())
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _u8ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+
+
+# --------------------------------------------------------------------------
+# Gate matrices (the oracle's own construction)
+# --------------------------------------------------------------------------
+
+_SQ2 = np.sqrt(0.5)
+_I2 = np.eye(2, dtype=np.complex128)
+_X = np.array([[0, 1], [1, 0]], dtype=np.complex128)
+_Y = np.array([[0, -1j], [1j, 0]], dtype=np.complex128)
+_Z = np.array([[1, 0], [0, -1]], dtype=np.complex128)
+_H = _SQ2 * np.array([[1, 1], [1, -1]], dtype=np.complex128)
+_S = np.array([[1, 0], [0, 1j]], dtype=np.complex128)
+T_GATE = np.array([[1, 0], [0, np.exp(1j * np.pi / 4)]], dtype=np.complex128)
+
+
+def clifford_table() -> np.ndarray:
+    """(24, 2, 2) complex128: C_k = P_(k mod 4) @ R_(k div 4)."""
+    paulis = (_I2, _X, _Y, _Z)
+    rots = (_I2, _H, _S, _S @ _H, _H @ _S, _H @ _S @ _H)
+    return np.array([paulis[k % 4] @ rots[k // 4] for k in range(24)])
+
+
+def gates(cliff: np.ndarray, tmask: np.ndarray, extra=None) -> np.ndarray:
+    """(d+1, n, 2, 2) complex128 slot gates U_(q,t) = T^tau . C_(cliff) [. extra].
+
+    ``extra`` is an optional (d+1, n, 2, 2) array applied after the Clifford
+    and T of each slot (None = identity)."""
+    cliff = np.asarray(cliff)
+    tmask = np.asarray(tmask)
+    d1, n = cliff.shape
+    tab = clifford_table()
+    u = tab[cliff.astype(np.int64)]
+    tm = np.zeros((d1, n), dtype=bool)
+    tm[: d1 - 1] = tmask.astype(bool)
+    u = np.where(tm[..., None, None], np.einsum("ab,tqbc->tqac", T_GATE, u), u)
+    if extra is not None:
+        u = np.einsum("tqab,tqbc->tqac", np.asarray(extra, np.complex128), u)
+    return np.ascontiguousarray(u)
+
+
+def circuit_gates(circ) -> np.ndarray:
+    return gates(circ.cliff, circ.tmask)
+
+
+def _flat(u: np.ndarray) -> np.ndarray:
+    u = np.ascontiguousarray(np.asarray(u, np.complex128))
+    return np.ascontiguousarray(u.view(np.float64).reshape(-1))
+
+
+# --------------------------------------------------------------------------
+# Amplitudes
+# --------------------------------------------------------------------------
+
+def sv_state(n: int, d: int, u: np.ndarray) -> np.ndarray:
+    """Full state U|0^n> (2^n complex128, basis index bit q = x_q)."""
+    lib = _load()
+    fu = _flat(u)
+    assert fu.size == (d + 1) * n * 8
+    out = np.empty(2 << n, np.float64)
+    rc = lib.tbo_sv_state(n, d, _dptr(fu), _dptr(out))
+    if rc:
+        raise RuntimeError(f"tbo_sv_state failed ({rc})")
+    return out.view(np.complex128)
+
+
+def basis_index(bits: np.ndarray) -> np.ndarray:
+    bits = np.atleast_2d(np.asarray(bits, np.int64))
+    return (bits << np.arange(bits.shape[1], dtype=np.int64)).sum(axis=1)
+
+
+def sv_amplitudes(n: int, d: int, u: np.ndarray, bits: np.ndarray) -> np.ndarray:
+    return sv_state(n, d, u)[basis_index(bits)]
+
+
+def nb_amplitudes(n: int, d: int, u: np.ndarray, bits: np.ndarray,
+                  return_peak: bool = False):
+    """Naive boundary contraction, one bitstring at a time."""
+    lib = _load()
+    fu = _flat(u)
+    assert fu.size == (d + 1) * n * 8
+    bits = np.ascontiguousarray(np.atleast_2d(bits).astype(np.uint8))
+    out = np.empty((bits.shape[0], 2), np.float64)
+    peak = ctypes.c_int(0)
+    peaks = []
+    for i in range(bits.shape[0]):
+        row = np.ascontiguousarray(bits[i])
+        o = np.empty(2, np.float64)
+        rc = lib.tbo_nb_amplitude(n, d, _dptr(fu), _u8ptr(row), _dptr(o), ctypes.byref(peak))
+        if rc:
+            raise RuntimeError(f"tbo_nb_amplitude failed ({rc})")
+        out[i] = o
+        peaks.append(peak.value)
+    amps = out.view(np.complex128).reshape(-1)
+    return (amps, max(peaks) if peaks else 0) if return_peak else amps
+
+
+def feynman_amplitude(n: int, d: int, u: np.ndarray, x) -> complex:
+    lib = _load()
+    fu = _flat(u)
+    xb = np.ascontiguousarray(np.asarray(x, np.uint8))
+    o = np.empty(2, np.float64)
+    rc = lib.tbo_feynman(n, d, _dptr(fu), _u8ptr(xb), _dptr(o))
+    if rc:
+        raise RuntimeError(f"tbo_feynman failed ({rc})")
+    return complex(o[0], o[1])
+
+
+def kron_state(n: int, d: int, u: np.ndarray) -> np.ndarray:
+    """U|0^n> from explicit 2^n x 2^n matrices: each slot is the Kronecker
+    product of its one-qubit gates, each CZ layer a diagonal +-1 matrix built
+    from the coupled pairs. Basis index bit q = qubit q, so qubit n-1 is the
+    leftmost Kronecker factor."""
+    u = np.asarray(u, np.complex128)
+    dim = 1 << n
+    idx = np.arange(dim)
+    state = np.zeros(dim, np.complex128)
+    state[0] = 1.0
+    for t in range(d + 1):
+        m = np.ones((1, 1), np.complex128)
+        for q in reversed(range(n)):
+            m = np.kron(m, u[t, q])
+        state = m @ state
+        if t < d:
+            diag = np.ones(dim)
+            for i0 in range(t % 2, n - 1, 2):
+                both = ((idx >> i0) & 1) & ((idx >> (i0 + 1)) & 1)
+                diag = diag * np.where(both == 1, -1.0, 1.0)
+            state = diag * state
+    return state
+
+
+def tableau_probability(circ, x) -> float:
+    """|<x|U|0^n>|^2 of a Clifford-only circuit (T gates must be absent)."""
+    if np.any(circ.tmask):
+        raise ValueError("tableau needs a Clifford-only circuit (no T)")
+    lib = _load()
+    cl = np.ascontiguousarray(circ.cliff.astype(np.uint8))
+    xb = np.ascontiguousarray(np.asarray(x, np.uint8))
+    p = ctypes.c_double(0.0)
+    rc = lib.tbo_tableau_prob(circ.n, circ.d, _u8ptr(cl), _u8ptr(xb), ctypes.byref(p))
+    if rc:
+        raise RuntimeError(f"tbo_tableau_prob failed ({rc})")
+    return float(p.value)
+
+
+def closed_form_hdiag(circ, bits: np.ndarray) -> np.ndarray:
+    """Exact amplitudes of an H / diagonal / H circuit.
+
+    With H on every qubit at slot 0 and slot d and only diagonal gates in
+    between (Cliffords I, Z, S, Z.S and T), everything between the two H layers
+    commutes and multiplies |y> by exp(i theta.y) (-1)^(sum_e m_e y_i y_(i+1)),
+    where theta_q collects the diagonal phases of qubit q and m_e is the parity
+    of the number of CZ layers on edge e. Hence
+        psi(x) = 2^-n sum_y exp(i theta.y) (-1)^(sum_e m_e y_i y_(i+1) + x.y),
+    evaluated with a 2x2 transfer matrix along the chain."""
+    n, d = circ.n, circ.d
+    tab = clifford_table()
+    cl = circ.cliff.astype(np.int64)
+    if not (np.all(cl[0] == 4) and np.all(cl[d] == 4)):
+        raise ValueError("slots 0 and d must be H on every qubit")
+    theta = np.zeros(n)
+    for t in range(1, d):
+        for q in range(n):
+            c = tab[cl[t, q]]
+            if abs(c[0, 1]) > 1e-12 or abs(c[1, 0]) > 1e-12 or abs(c[0, 0] - 1) > 1e-12:
+                raise ValueError("interior slots must be diagonal with (0,0) entry 1")
+            theta[q] += np.angle(c[1, 1])
+    theta += (np.pi / 4) * circ.tmask.sum(axis=0)
+    m = np.array([sum(1 for l in range(d) if l % 2 == i % 2) % 2 for i in range(n - 1)])
+    bits = np.atleast_2d(bits)
+    out = np.empty(bits.shape[0], np.complex128)
+    for b, x in enumerate(bits):
+        ph = np.exp(1j * theta) * np.where(x == 1, -1.0, 1.0)
+        v = np.array([1.0 + 0j, ph[0]])
+        for q in range(1, n):
+            s = -1.0 if m[q - 1] else 1.0
+            v = np.array([v[0] + v[1], (v[0] + s * v[1]) * ph[q]])
+        out[b] = (v[0] + v[1]) / (2.0 ** n)
+    return out
+
+
+EULER_GAMMA = 0.57721566490153286060651209
+
+
+def log_xeb(amps: np.ndarray, n: int) -> float:
+    """F = gamma + n ln 2 + (1/N) sum_i ln p(x_i), p = |psi|^2 (Sec. 5.2, normalized log-XEB equation)."""
+    p = np.abs(np.asarray(amps, np.complex128)) ** 2
+    return float(EULER_GAMMA + n * np.log(2.0) + np.mean(np.log(p)))
+
+
+def rel_l2(a: np.ndarray, ref: np.ndarray) -> float:
+    """||a - ref||_2 / ||ref||_2 over a batch."""
+    a = np.asarray(a, np.complex128)
+    ref = np.asarray(ref, np.complex128)
+    return float(np.linalg.norm(a - ref) / np.linalg.norm(ref))
+
+
+if __name__ == "__main__":  # pragma: no cover
+    build(force="--force" in sys.argv)
+    print(_LIB_PATH)
