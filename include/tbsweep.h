@@ -1,0 +1,179 @@
+/*
+ * tbsweep -- exact amplitudes of open-boundary 1D brickwork circuits by the
+ * temporal-boundary sweep, on one NVIDIA GB300 (sm_103a).
+ *
+ * The method (arXiv 2608.13110, Sec. 3.1, Algorithm 1 and Proposition 1):
+ * the circuit's tensor network (Sec. 2.2) is contracted one qubit row at a
+ * time. The running "temporal state" B holds 2^h complex64 entries,
+ * h = ceil(d/2), one address bit per CZ layer in which the last absorbed row
+ * still waits for its partner. Absorbing a row is a staircase of h paired
+ * steps (consume one stored bit, create the next one), each a controlled 2x2
+ * complex gate on two adjacent address bits; rows alternate time direction
+ * (snake order) so that the width stays h.
+ *
+ * Circuit convention: qubits q = 0..n-1, CZ layers l = 0..d-1, layer l acts
+ * on (i, i+1) for every i = l (mod 2) with i+1 < n (Sec. 2.1); one-qubit
+ * slots t = 0..d, slot t < d before CZ layer t and slot d after the last
+ * layer; the gate of slot t on qubit q is U = E . T^tau . C, with C one of the
+ * 24 Cliffords C_k = P_(k mod 4) . R_(k div 4), P in (I, X, Y, Z),
+ * Y = [[0,-i],[i,0]], R in (I, H, S, S.H, H.S, H.S.H), T = diag(1, e^(i pi/4))
+ * and E an optional arbitrary extra gate. Output: psi(x) = <x|U|0^n>, with
+ * bit q of a bitstring the value of qubit q (Sec. 2.2).
+ *
+ * All functions return a tb_status code and never throw. Unless stated
+ * otherwise, every pointer argument must be non-NULL.
+ */
+#ifndef TBSWEEP_H
+#define TBSWEEP_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TB_API __attribute__((visibility("default")))
+#else
+#define TB_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+enum tb_status {
+    TB_OK = 0,
+    TB_EINVAL = 1,   /* NULL pointer, bit not in {0,1}, Clifford index > 23, bad size */
+    TB_EDOMAIN = 2,  /* circuit outside what this build contracts: n < 2, d odd or
+                        < 2, ceil(d/2) > 40 for a plan, > 33 for evaluation */
+    TB_ENOMEM = 3,   /* workspace smaller than tb_workspace_bytes() or host allocation failed */
+    TB_ECUDA = 4,    /* a CUDA runtime call failed; tb_last_error() has the message */
+    TB_ETIMEOUT = 5  /* reserved for bounded device waits */
+};
+
+/* Opaque plan: the folded gates, the step tables and the pass schedule of one
+ * circuit. Immutable after creation; safe to share between threads. */
+typedef struct tb_plan tb_plan;
+
+/* One arbitrary one-qubit gate, applied after the Clifford and T of its slot.
+ * m: row-major 2x2 complex matrix as (re, im) pairs: m[0..1] = (0,0),
+ * m[2..3] = (0,1), m[4..5] = (1,0), m[6..7] = (1,1). */
+typedef struct {
+    int32_t qubit; /* 0..n-1 */
+    int32_t slot;  /* 0..d   */
+    double m[8];
+} tb_gate1q;
+
+/* Plan options. A zeroed struct (or NULL) selects the defaults. */
+typedef struct {
+    int32_t window_bits;  /* largest number of address bits one boundary pass
+                             covers (5..10; 0 = default 10) */
+    int32_t bottom_bits;  /* size of the window at address bit 0 (5..10; 0 = auto) */
+    int32_t top_bits;     /* size of the window ending at bit h-1 (5..10; 0 = auto) */
+    int32_t reserved;
+    int64_t hbm_budget_bytes; /* cap on the boundary batch a call keeps on the
+                                 device (0 = no cap beyond the workspace) */
+} tb_opts;
+
+/* Plan summary. */
+typedef struct {
+    int32_t n, d;
+    int32_t width;          /* W of Algorithm 1's path, log2 of the largest
+                               intermediate (Sec. 2.2 contraction width) */
+    int32_t boundary_bits;  /* h: the device boundary holds 2^h complex64 */
+    double log2_cost;       /* log2 C, C = sum over Algorithm 1's pairwise
+                               contractions of |I||J||K| (Sec. 2.2) */
+    int64_t boundary_bytes; /* 8 * 2^h */
+    int32_t n_steps;        /* paired steps on the device (rows 1..n-2) */
+    int32_t n_passes;       /* HBM passes over the boundary per amplitude
+                               (0 when the whole boundary fits one CTA) */
+    int64_t table_bytes;    /* device bytes of the plan's tables */
+} tb_plan_info_t;
+
+/* Create a plan (host only: no CUDA call is made).
+ *   n, d   : qubits and CZ layers; n >= 2, d even, 2 <= d, ceil(d/2) <= 40
+ *            (else TB_EDOMAIN). Plans wider than 33 bits (2^33 complex64 =
+ *            64 GiB) only report their counters: evaluating them returns
+ *            TB_EDOMAIN and tb_workspace_bytes returns -1.
+ *   cliff  : (d+1)*n Clifford indices 0..23, slot-major (cliff[t*n + q]);
+ *            NULL means identity everywhere.
+ *   tmask  : d*n bytes in {0,1}, tmask[t*n + q] = 1 puts a T after the
+ *            Clifford of slot t < d; NULL means no T gate.
+ *   extra  : n_extra arbitrary gates (may be NULL when n_extra == 0).
+ *   opts   : NULL or a tb_opts (zero fields = defaults).
+ *   out    : receives the plan; release it with tb_plan_destroy.
+ * The input arrays are copied; the caller keeps ownership. */
+TB_API int tb_plan_create(int n, int d, const uint8_t* cliff, const uint8_t* tmask,
+                   const tb_gate1q* extra, int n_extra, const tb_opts* opts,
+                   tb_plan** out);
+
+/* Fill *info. */
+TB_API int tb_plan_info(const tb_plan* plan, tb_plan_info_t* info);
+
+/* Device workspace bytes that tb_amplitudes / tb_amplitudes_device need to
+ * evaluate nb bitstrings (tables, rescaling state, partial sums and one
+ * boundary per bitstring evaluated concurrently). Returns -1 on a bad
+ * argument. The batch a call evaluates concurrently is the largest that fits
+ * the workspace given (and the plan's hbm_budget_bytes). */
+TB_API int64_t tb_workspace_bytes(const tb_plan* plan, int64_t nb);
+
+/* Smallest workspace that can evaluate any number of bitstrings (one
+ * boundary at a time). */
+TB_API int64_t tb_workspace_min_bytes(const tb_plan* plan);
+
+/* Copy the plan's tables into the head of a device workspace, on stream
+ * (asynchronous with respect to the host for pinned memory; the plan's host
+ * tables must outlive the copy, which they do while the plan lives).
+ *   d_ws  : caller-owned device memory, at least tb_workspace_min_bytes().
+ *   stream: a cudaStream_t, or NULL for the legacy default stream. */
+TB_API int tb_plan_upload(const tb_plan* plan, void* d_ws, int64_t ws_bytes, void* stream);
+
+/* Amplitudes from device-resident inputs, fully asynchronous on stream.
+ *   d_bits: device, nb*n bytes, d_bits[i*n + q] = x_q in {0,1} (values are
+ *           not checked on the device; anything nonzero counts as 1).
+ *   d_ws  : workspace that tb_plan_upload filled for this plan.
+ *   d_out : device, 2*nb doubles, (re, im) of psi(x_i) in FP64.
+ * Work is enqueued only; no synchronisation. */
+TB_API int tb_amplitudes_device(const tb_plan* plan, const uint8_t* d_bits, int64_t nb,
+                         void* d_ws, int64_t ws_bytes, double* d_out, void* stream);
+
+/* Amplitudes end to end from host buffers: uploads the tables, copies the
+ * bitstrings host->device, runs the sweep, copies the amplitudes back and
+ * synchronises the stream before returning.
+ *   bits : host, nb*n bytes in {0,1} (checked: TB_EINVAL otherwise).
+ *   d_ws : caller-owned device workspace of at least
+ *          tb_workspace_min_bytes() + nb*(n + 16) bytes rounded up; it also
+ *          holds the staged inputs and outputs.
+ *   out  : host, 2*nb doubles (re, im). */
+TB_API int tb_amplitudes(const tb_plan* plan, const uint8_t* bits, int64_t nb, void* d_ws,
+                  int64_t ws_bytes, double* out, void* stream);
+
+/* The pass schedule: for pass i, sched[3*i] = shape (0 forward window,
+ * 1 reversed window, 2 turn at the top, 3 turn at address bit 0, 4 first
+ * window of the first absorbed row, 5 last window of a reversed last row,
+ * 6 last window of a forward last row), sched[3*i+1] = window bits M,
+ * sched[3*i+2] = address bit of the window's lowest bit. Writes at most cap
+ * passes (sched may be NULL when cap == 0) and returns the number of passes,
+ * or -1 for a NULL plan. */
+TB_API int tb_plan_schedule(const tb_plan* plan, int32_t* sched, int cap);
+
+/* log-XEB estimator F = gamma + n ln 2 + (1/N) sum_i ln |amp_i|^2 (Sec. 5.2,
+ * normalized log-XEB equation), host FP64. amp: 2*nb doubles (re, im).
+ * A zero amplitude gives -inf. */
+TB_API int tb_log_xeb(const double* amp, int64_t nb, int n, double* out);
+
+/* The Clifford table this library uses: m receives C_k as in tb_gate1q. */
+TB_API int tb_clifford_matrix(int k, double m[8]);
+
+/* Release a plan (NULL is ignored). */
+TB_API void tb_plan_destroy(tb_plan* plan);
+
+/* Static description of a status code. */
+TB_API const char* tb_status_str(int status);
+
+/* Message of the last failed call on this host thread ("" if none). */
+TB_API const char* tb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TBSWEEP_H */

@@ -1,0 +1,229 @@
+"""GB300 (sm_103a) temporal-boundary sweep for exact amplitudes of open 1D
+brickwork circuits (arXiv 2608.13110, Sec. 3.1, Algorithm 1).
+
+Thin ctypes binding over ``libtbsweep.so`` (C-ABI in ``include/tbsweep.h``):
+argument marshalling only, every step of the sweep runs in the library's CUDA
+kernels. PyTorch supplies device memory and streams. There is no CPU
+fallback: if the library is missing, importing this package raises.
+
+Usage::
+
+    import paper_2608_13110_gb300 as tb
+    plan = tb.Plan(n, d, cliff, tmask)          # host planner (no GPU needed)
+    amps = plan.amplitudes(bits)                # host in / host out, complex128
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtbsweep.so")
+
+TB_OK, TB_EINVAL, TB_EDOMAIN, TB_ENOMEM, TB_ECUDA, TB_ETIMEOUT = range(6)
+
+class _Gate1q(ctypes.Structure):
+    _fields_ = [("qubit", ctypes.c_int32), ("slot", ctypes.c_int32), ("m", ctypes.c_double * 8)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("window_bits", ctypes.c_int32), ("bottom_bits", ctypes.c_int32),
+                ("top_bits", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("hbm_budget_bytes", ctypes.c_int64)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("d", ctypes.c_int32), ("width", ctypes.c_int32),
+                ("boundary_bits", ctypes.c_int32), ("log2_cost", ctypes.c_double),
+                ("boundary_bytes", ctypes.c_int64), ("n_steps", ctypes.c_int32),
+                ("n_passes", ctypes.c_int32), ("table_bytes", ctypes.c_int64)]
+
+
+_vp = ctypes.c_void_p
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+_dp = ctypes.POINTER(ctypes.c_double)
+_sig = {
+    "tb_plan_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _u8p, _u8p, ctypes.POINTER(_Gate1q),
+                                      ctypes.c_int, ctypes.POINTER(_Opts), ctypes.POINTER(_vp)]),
+    "tb_plan_info": (ctypes.c_int, [_vp, ctypes.POINTER(_Info)]),
+    "tb_workspace_bytes": (ctypes.c_int64, [_vp, ctypes.c_int64]),
+    "tb_workspace_min_bytes": (ctypes.c_int64, [_vp]),
+    "tb_plan_upload": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _vp]),
+    "tb_amplitudes_device": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _vp, ctypes.c_int64, _vp, _vp]),
+    "tb_amplitudes": (ctypes.c_int, [_vp, _u8p, ctypes.c_int64, _vp, ctypes.c_int64, _dp, _vp]),
+    "tb_plan_schedule": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int32), ctypes.c_int]),
+    "tb_log_xeb": (ctypes.c_int, [_dp, ctypes.c_int64, ctypes.c_int, _dp]),
+    "tb_clifford_matrix": (ctypes.c_int, [ctypes.c_int, _dp]),
+    "tb_plan_destroy": (None, [_vp]),
+    "tb_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "tb_last_error": (ctypes.c_char_p, []),
+}
+
+class _Lib:
+    """The CUDA library, loaded on first use. A missing library is an error:
+    there is no CPU fallback."""
+
+    def __init__(self):
+        self._dll = None
+
+    def _load(self):
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(
+                f"{LIB_PATH} is missing: build it with `python -m paper_2608_13110_gb300.build` "
+                "(there is no CPU fallback)")
+        dll = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _sig.items():
+            f = getattr(dll, name)
+            f.restype = res
+            f.argtypes = args
+        self._dll = dll
+
+    def __getattr__(self, name):
+        if self._dll is None:
+            self._load()
+        return getattr(self._dll, name)
+
+
+_lib = _Lib()
+
+EXPORTED = tuple(_sig)
+
+
+class TbError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _lib.tb_last_error().decode() or _lib.tb_status_str(status).decode()
+        super().__init__(f"{where}: {_lib.tb_status_str(status).decode()} ({msg})")
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != TB_OK:
+        raise TbError(rc, where)
+
+
+def _u8(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.uint8))
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+class Plan:
+    """A planned circuit: folded gates, step tables and pass schedule.
+
+    cliff: (d+1, n) Clifford indices (None = identity); tmask: (d, n) 0/1
+    (None = no T); extra: iterable of (qubit, slot, 2x2 complex matrix)."""
+
+    def __init__(self, n: int, d: int, cliff=None, tmask=None, extra=None, *,
+                 window_bits: int = 0, bottom_bits: int = 0, top_bits: int = 0,
+                 hbm_budget_bytes: int = 0):
+        self.n, self.d = int(n), int(d)
+        self._cliff = None if cliff is None else _u8(cliff).reshape(-1)
+        self._tmask = None if tmask is None else _u8(tmask).reshape(-1)
+        if self._cliff is not None and self._cliff.size != (d + 1) * n:
+            raise ValueError("cliff must have (d+1)*n entries")
+        if self._tmask is not None and self._tmask.size != d * n:
+            raise ValueError("tmask must have d*n entries")
+        ex = list(extra or [])
+        arr = (_Gate1q * max(1, len(ex)))()
+        for i, (q, t, m) in enumerate(ex):
+            m = np.asarray(m, np.complex128).reshape(2, 2)
+            arr[i].qubit, arr[i].slot = int(q), int(t)
+            for k, z in enumerate(m.reshape(-1)):
+                arr[i].m[2 * k] = z.real
+                arr[i].m[2 * k + 1] = z.imag
+        opts = _Opts(window_bits, bottom_bits, top_bits, 0, hbm_budget_bytes)
+        h = _vp()
+        cp = None if self._cliff is None else self._cliff.ctypes.data_as(_u8p)
+        tp = None if self._tmask is None else self._tmask.ctypes.data_as(_u8p)
+        _check(_lib.tb_plan_create(self.n, self.d, cp, tp, arr if ex else None, len(ex),
+                                   ctypes.byref(opts), ctypes.byref(h)), "tb_plan_create")
+        self._h = h
+
+    @classmethod
+    def from_circuit(cls, circ, **kw) -> "Plan":
+        return cls(circ.n, circ.d, circ.cliff, circ.tmask, **kw)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.tb_plan_destroy(h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def info(self) -> dict:
+        inf = _Info()
+        _check(_lib.tb_plan_info(self._h, ctypes.byref(inf)), "tb_plan_info")
+        return {f: getattr(inf, f) for f, _ in _Info._fields_}
+
+    PASS_SHAPES = ("fwd", "rev", "top", "bot", "bot_start", "bot_end", "top_end")
+
+    @property
+    def schedule(self) -> list:
+        """[(shape, window_bits, low_address_bit)] for every HBM pass."""
+        npass = _lib.tb_plan_schedule(self._h, None, 0)
+        buf = (ctypes.c_int32 * max(1, 3 * npass))()
+        _lib.tb_plan_schedule(self._h, buf, npass)
+        return [(self.PASS_SHAPES[buf[3 * i]], buf[3 * i + 1], buf[3 * i + 2]) for i in range(npass)]
+
+    def workspace_bytes(self, nb: int) -> int:
+        v = _lib.tb_workspace_bytes(self._h, int(nb))
+        if v < 0:
+            raise ValueError("bad nb")
+        return int(v)
+
+    def workspace_min_bytes(self) -> int:
+        return int(_lib.tb_workspace_min_bytes(self._h))
+
+    def alloc_workspace(self, nb: int, device="cuda"):
+        import torch
+        return torch.empty(self.workspace_bytes(nb), dtype=torch.uint8, device=device)
+
+    def upload(self, ws, stream=None) -> None:
+        _check(_lib.tb_plan_upload(self._h, ws.data_ptr(), ws.numel(), _stream_handle(stream)),
+               "tb_plan_upload")
+
+    def amplitudes_device(self, d_bits, ws, d_out, stream=None) -> None:
+        """Enqueue the sweep: d_bits (nb, n) uint8 and d_out (nb, 2) float64 are
+        CUDA tensors; ``ws`` must hold this plan's tables (``upload``)."""
+        nb = d_bits.shape[0] if d_bits.dim() > 1 else d_bits.numel() // self.n
+        _check(_lib.tb_amplitudes_device(self._h, d_bits.data_ptr(), nb, ws.data_ptr(), ws.numel(),
+                                         d_out.data_ptr(), _stream_handle(stream)),
+               "tb_amplitudes_device")
+
+    def amplitudes(self, bits, ws=None, stream=None, out=None) -> np.ndarray:
+        """Host bitstrings (nb, n) -> host complex128 amplitudes; synchronous."""
+        b = _u8(bits)
+        if b.ndim == 1:
+            b = b.reshape(1, -1)
+        nb = b.shape[0]
+        if out is None:
+            out = np.empty((nb, 2), np.float64)
+        if ws is None:
+            ws = self.alloc_workspace(nb)
+        _check(_lib.tb_amplitudes(self._h, b.ctypes.data_as(_u8p), nb, ws.data_ptr(), ws.numel(),
+                                  out.ctypes.data_as(_dp), _stream_handle(stream)), "tb_amplitudes")
+        return out.view(np.complex128).reshape(-1)
+
+
+def log_xeb(amps, n: int) -> float:
+    a = np.ascontiguousarray(np.asarray(amps, np.complex128)).view(np.float64)
+    out = ctypes.c_double(0.0)
+    _check(_lib.tb_log_xeb(a.ctypes.data_as(_dp), a.size // 2, int(n), ctypes.byref(out)), "tb_log_xeb")
+    return float(out.value)
+
+
+def clifford_matrix(k: int) -> np.ndarray:
+    m = np.empty(8, np.float64)
+    _check(_lib.tb_clifford_matrix(int(k), m.ctypes.data_as(_dp)), "tb_clifford_matrix")
+    return m.view(np.complex128).reshape(2, 2)

@@ -1,0 +1,369 @@
+// C-ABI of the temporal-boundary sweep (declared in include/tbsweep.h).
+//
+// Workspace layout of one call (all offsets 256-byte aligned):
+//   [tables of the plan][host staging: bits, amplitudes (tb_amplitudes only)]
+//   [per batch element: rescaling slots | reduction partials | boundary]
+// The boundary of one bitstring is 2^h complex64 entries; several bitstrings
+// are evaluated side by side when the workspace holds several boundaries.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+
+#include "misc_kernels.cuh"
+#include "pass_kernel.cuh"
+#include "tb_plan.h"
+#include "tbsweep.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+#define TB_CUDA(call)                                                                   \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(TB_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+using namespace tb;
+
+constexpr int64_t DEFAULT_BATCH_ENTRIES = (int64_t)1 << 30;  // 8 GiB of boundaries
+
+struct CallLayout {
+    int nslots = 0;
+    int64_t scale_bytes = 0;    // per batch element
+    int red_blocks = 0;         // reduction blocks per batch element
+    int64_t partial_bytes = 0;  // per batch element
+    int64_t boundary_bytes = 0; // per batch element
+    int64_t per_b = 0;
+};
+
+bool small_path(const Plan& P) { return P.h <= SMALL_H_MAX; }
+
+CallLayout call_layout(const Plan& P) {
+    CallLayout c;
+    if (small_path(P)) return c;
+    c.nslots = (int)P.passes.size() + 2;
+    c.scale_bytes = align_up((int64_t)c.nslots * 8, 256);
+    const int64_t nchunks = (int64_t)1 << (P.h - P.k);
+    c.red_blocks = (int)std::min<int64_t>(nchunks, MAX_RED_BLOCKS);
+    c.partial_bytes = align_up((int64_t)c.red_blocks * 16, 256);
+    c.boundary_bytes = (int64_t)8 << P.h;
+    c.per_b = c.scale_bytes + c.partial_bytes + c.boundary_bytes;
+    return c;
+}
+
+int64_t staging_bytes(const Plan& P, int64_t nb) {
+    return align_up(nb * P.n, 256) + align_up(nb * 16, 256);
+}
+
+int64_t max_batch(const Plan& P, const CallLayout& c) {
+    if (c.per_b == 0) return INT64_MAX;
+    int64_t mb = std::max<int64_t>(1, DEFAULT_BATCH_ENTRIES >> P.h);
+    if (P.opts.hbm_budget_bytes > 0) mb = std::min(mb, std::max<int64_t>(1, P.opts.hbm_budget_bytes / c.per_b));
+    return mb;
+}
+
+int num_sms() {
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+    if (!cached[dev]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
+        cached[dev] = v;
+    }
+    return cached[dev];
+}
+
+cudaError_t launch_pass(const PassDesc& d, const PassParams& p, int grid, cudaStream_t st) {
+    switch (d.type) {
+        case P_FWD: return launch_pass_t0(d.M, p, grid, st);
+        case P_REV: return launch_pass_t1(d.M, p, grid, st);
+        case P_TOP: return launch_pass_t2(d.M, p, grid, st);
+        case P_BOT: return launch_pass_t3(d.M, p, grid, st);
+        case P_BOT_START: return launch_pass_t4(d.M, p, grid, st);
+        case P_BOT_END: return launch_pass_t5(d.M, p, grid, st);
+        case P_TOP_END: return launch_pass_t6(d.M, p, grid, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <class T>
+const T* tab(const void* ws, int64_t off) {
+    return reinterpret_cast<const T*>(static_cast<const uint8_t*>(ws) + off);
+}
+
+// Enqueue the sweep for nb bitstrings already on the device.
+int run_device(const Plan& P, const uint8_t* d_bits, int64_t nb, void* d_ws, int64_t ws_bytes,
+               int64_t region_off, double* d_out, cudaStream_t st) {
+    const TableLayout& L = P.lay;
+    if (small_path(P)) {
+        SmallParams sp;
+        sp.n = P.n;
+        sp.h = P.h;
+        sp.bits = d_bits;
+        sp.steps = tab<StepG>(d_ws, L.steps);
+        sp.tgt = tab<int8_t>(d_ws, L.step_tgt);
+        sp.ctl = tab<int8_t>(d_ws, L.step_ctl);
+        sp.xq = tab<int16_t>(d_ws, L.step_xq);
+        sp.row_end = tab<int32_t>(d_ws, L.row_end);
+        sp.nrows = (int)P.row_end.size();
+        sp.init_low = tab<float2>(d_ws, L.init_low);
+        sp.init_top = tab<float2>(d_ws, L.init_top);
+        sp.red_low = tab<float2>(d_ws, L.red_low);
+        const int64_t chunk = 1 << 30;
+        for (int64_t b0 = 0; b0 < nb; b0 += chunk) {
+            sp.nb = (int)std::min(chunk, nb - b0);
+            sp.bits = d_bits + b0 * P.n;
+            sp.out = d_out + 2 * b0;
+            TB_CUDA(launch_small(sp, st));
+        }
+        return TB_OK;
+    }
+    const CallLayout c = call_layout(P);
+    const int64_t avail = ws_bytes - region_off;
+    int64_t batch = std::min<int64_t>(nb, avail / c.per_b);
+    batch = std::min(batch, max_batch(P, c));
+    if (batch < 1)
+        return fail(TB_ENOMEM, "workspace too small: need at least " +
+                                   std::to_string(region_off + c.per_b) + " bytes");
+    uint8_t* region = static_cast<uint8_t*>(d_ws) + region_off;
+    uint8_t* scales = region;
+    double2* partials = reinterpret_cast<double2*>(region + batch * c.scale_bytes);
+    float2* boundary = reinterpret_cast<float2*>(region + batch * (c.scale_bytes + c.partial_bytes));
+    uint32_t* maxs = reinterpret_cast<uint32_t*>(scales);
+    int32_t* exps = reinterpret_cast<int32_t*>(scales) + c.nslots;
+    const int64_t sstride = c.scale_bytes / 4;
+    const int64_t b_stride = (int64_t)1 << P.h;
+    const int nsm = num_sms();
+    const StepG* steps = tab<StepG>(d_ws, L.steps);
+
+    for (int64_t b0 = 0; b0 < nb; b0 += batch) {
+        const int nbat = (int)std::min<int64_t>(batch, nb - b0);
+        const uint8_t* bits = d_bits + b0 * P.n;
+        TB_CUDA(cudaMemsetAsync(scales, 0, (size_t)(nbat * c.scale_bytes), st));
+
+        InitParams ip;
+        ip.B = boundary;
+        ip.b_stride = b_stride;
+        ip.h = P.h; ip.k = P.k; ip.m = P.m; ip.top = P.top; ip.n = P.n;
+        ip.chunk_shift = P.h - P.k;
+        ip.nchunks = (int64_t)nbat << ip.chunk_shift;
+        ip.bits = bits;
+        ip.low = tab<float2>(d_ws, L.init_low);
+        ip.mid = tab<float2>(d_ws, L.init_mid);
+        ip.topt = tab<float2>(d_ws, L.init_top);
+        ip.maxs = maxs;
+        ip.sstride = sstride;
+        TB_CUDA(launch_init(ip, (int)std::min<int64_t>(ip.nchunks, 8LL * nsm), st));
+
+        for (size_t k = 0; k < P.passes.size(); ++k) {
+            const PassDesc& d = P.passes[k];
+            PassParams pp;
+            pp.B = boundary;
+            pp.b_stride = b_stride;
+            pp.h = P.h; pp.lo = d.lo; pp.n = P.n;
+            pp.tile_shift = P.h - TILE_BITS;
+            pp.ntiles = (int64_t)nbat << pp.tile_shift;
+            pp.steps = steps + d.step0;
+            pp.xs_step0 = d.xs_step[0]; pp.xs_q0 = d.xs_q[0];
+            pp.xs_step1 = d.xs_step[1]; pp.xs_q1 = d.xs_q[1];
+            pp.bits = bits;
+            pp.maxs = maxs;
+            pp.exps = exps;
+            pp.sstride = sstride;
+            pp.slot = (int)k;
+            const int grid = (int)std::min<int64_t>(pp.ntiles, nsm);  // one persistent CTA per SM
+            TB_CUDA(launch_pass(d, pp, grid, st));
+        }
+
+        ReduceParams rp;
+        rp.B = boundary;
+        rp.b_stride = b_stride;
+        rp.h = P.h; rp.k = P.k; rp.m = P.m; rp.top = P.top; rp.n = P.n;
+        rp.chunk_shift = P.h - P.k;
+        rp.blocks_per_b = c.red_blocks;
+        rp.nbatch = nbat;
+        rp.bits = bits;
+        rp.low = tab<float2>(d_ws, L.red_low);
+        rp.mid = tab<float2>(d_ws, L.red_mid);
+        rp.topt = tab<float2>(d_ws, L.red_top);
+        rp.maxs = maxs;
+        rp.exps = exps;
+        rp.sstride = sstride;
+        rp.slot = (int)P.passes.size();
+        rp.partials = partials;
+        TB_CUDA(launch_reduce(rp, st));
+
+        FinalizeParams fp;
+        fp.partials = partials;
+        fp.blocks_per_b = c.red_blocks;
+        fp.exps = exps;
+        fp.sstride = sstride;
+        fp.nslots = c.nslots;
+        fp.nbatch = nbat;
+        fp.out = d_out + 2 * b0;
+        TB_CUDA(launch_finalize(fp, st));
+    }
+    return TB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tb_plan_create(int n, int d, const uint8_t* cliff, const uint8_t* tmask, const tb_gate1q* extra,
+                   int n_extra, const tb_opts* opts, tb_plan** out) {
+    if (!out) return fail(TB_EINVAL, "out is NULL");
+    *out = nullptr;
+    try {
+        tb_plan* p = new tb_plan;
+        std::string err;
+        const int rc = plan_build(p->p, n, d, cliff, tmask, extra, n_extra, opts, err);
+        if (rc != TB_OK) {
+            delete p;
+            return fail(rc, err);
+        }
+        *out = p;
+        return TB_OK;
+    } catch (const std::bad_alloc&) {
+        return fail(TB_ENOMEM, "host allocation failed");
+    } catch (...) {
+        return fail(TB_EINVAL, "plan construction failed");
+    }
+}
+
+int tb_plan_info(const tb_plan* plan, tb_plan_info_t* info) {
+    if (!plan || !info) return fail(TB_EINVAL, "NULL argument");
+    const Plan& P = plan->p;
+    std::memset(info, 0, sizeof(*info));
+    info->n = P.n;
+    info->d = P.d;
+    info->width = P.width;
+    info->boundary_bits = P.h;
+    info->log2_cost = P.log2cost;
+    info->boundary_bytes = (int64_t)8 << P.h;
+    info->n_steps = (int)P.steps.size();
+    info->n_passes = (int)P.passes.size();
+    info->table_bytes = P.lay.total;
+    return TB_OK;
+}
+
+int tb_plan_schedule(const tb_plan* plan, int32_t* sched, int cap) {
+    if (!plan) return -1;
+    const Plan& P = plan->p;
+    const int np = (int)P.passes.size();
+    for (int i = 0; i < np && i < cap && sched; ++i) {
+        sched[3 * i] = P.passes[i].type;
+        sched[3 * i + 1] = P.passes[i].M;
+        sched[3 * i + 2] = P.passes[i].lo;
+    }
+    return np;
+}
+
+int64_t tb_workspace_bytes(const tb_plan* plan, int64_t nb) {
+    if (!plan || nb < 0) return -1;
+    const Plan& P = plan->p;
+    if (P.h > MAX_H) return -1;
+    const CallLayout c = call_layout(P);
+    const int64_t batch = std::max<int64_t>(1, std::min<int64_t>(nb, max_batch(P, c)));
+    return P.lay.total + staging_bytes(P, nb) + (c.per_b ? batch * c.per_b : 0);
+}
+
+int64_t tb_workspace_min_bytes(const tb_plan* plan) {
+    if (!plan) return -1;
+    const Plan& P = plan->p;
+    if (P.h > MAX_H) return -1;
+    return P.lay.total + call_layout(P).per_b;
+}
+
+int tb_plan_upload(const tb_plan* plan, void* d_ws, int64_t ws_bytes, void* stream) {
+    if (!plan || !d_ws) return fail(TB_EINVAL, "NULL argument");
+    const Plan& P = plan->p;
+    if (P.h > MAX_H) return fail(TB_EDOMAIN, "boundary wider than 2^33 entries");
+    if (ws_bytes < P.lay.total) return fail(TB_ENOMEM, "workspace smaller than the plan's tables");
+    TB_CUDA(cudaMemcpyAsync(d_ws, P.blob.data(), (size_t)P.lay.total, cudaMemcpyHostToDevice,
+                            static_cast<cudaStream_t>(stream)));
+    return TB_OK;
+}
+
+int tb_amplitudes_device(const tb_plan* plan, const uint8_t* d_bits, int64_t nb, void* d_ws,
+                         int64_t ws_bytes, double* d_out, void* stream) {
+    if (!plan || !d_ws || (nb > 0 && (!d_bits || !d_out)) || nb < 0)
+        return fail(TB_EINVAL, "NULL or negative argument");
+    const Plan& P = plan->p;
+    if (P.h > MAX_H) return fail(TB_EDOMAIN, "boundary wider than 2^33 entries");
+    if (nb == 0) return TB_OK;
+    if (ws_bytes < P.lay.total) return fail(TB_ENOMEM, "workspace smaller than the plan's tables");
+    return run_device(P, d_bits, nb, d_ws, ws_bytes, P.lay.total, d_out, static_cast<cudaStream_t>(stream));
+}
+
+int tb_amplitudes(const tb_plan* plan, const uint8_t* bits, int64_t nb, void* d_ws, int64_t ws_bytes,
+                  double* out, void* stream) {
+    if (!plan || !d_ws || nb < 0 || (nb > 0 && (!bits || !out)))
+        return fail(TB_EINVAL, "NULL or negative argument");
+    const Plan& P = plan->p;
+    if (P.h > MAX_H) return fail(TB_EDOMAIN, "boundary wider than 2^33 entries");
+    if (nb == 0) return TB_OK;
+    for (int64_t i = 0; i < nb * P.n; ++i)
+        if (bits[i] > 1) return fail(TB_EINVAL, "bitstring entries must be 0 or 1");
+    const int64_t stage = staging_bytes(P, nb);
+    if (ws_bytes < P.lay.total + stage) return fail(TB_ENOMEM, "workspace too small for the staged inputs");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint8_t* ws = static_cast<uint8_t*>(d_ws);
+    uint8_t* d_bits = ws + P.lay.total;
+    double* d_out = reinterpret_cast<double*>(ws + P.lay.total + align_up(nb * P.n, 256));
+    TB_CUDA(cudaMemcpyAsync(d_ws, P.blob.data(), (size_t)P.lay.total, cudaMemcpyHostToDevice, st));
+    TB_CUDA(cudaMemcpyAsync(d_bits, bits, (size_t)(nb * P.n), cudaMemcpyHostToDevice, st));
+    const int rc = run_device(P, d_bits, nb, d_ws, ws_bytes, P.lay.total + stage, d_out, st);
+    if (rc != TB_OK) return rc;
+    TB_CUDA(cudaMemcpyAsync(out, d_out, (size_t)(16 * nb), cudaMemcpyDeviceToHost, st));
+    TB_CUDA(cudaStreamSynchronize(st));
+    return TB_OK;
+}
+
+int tb_log_xeb(const double* amp, int64_t nb, int n, double* out) {
+    if (!amp || !out || nb <= 0 || n < 1) return fail(TB_EINVAL, "bad argument");
+    const double gamma = 0.57721566490153286060651209;
+    double s = 0.0;
+    for (int64_t i = 0; i < nb; ++i) s += std::log(amp[2 * i] * amp[2 * i] + amp[2 * i + 1] * amp[2 * i + 1]);
+    *out = gamma + n * std::log(2.0) + s / (double)nb;
+    return TB_OK;
+}
+
+int tb_clifford_matrix(int k, double m[8]) {
+    if (k < 0 || k > 23 || !m) return fail(TB_EINVAL, "index must be 0..23");
+    const M2 c = clifford(k);
+    for (int i = 0; i < 4; ++i) {
+        m[2 * i] = c.a[i].real();
+        m[2 * i + 1] = c.a[i].imag();
+    }
+    return TB_OK;
+}
+
+void tb_plan_destroy(tb_plan* plan) { delete plan; }
+
+const char* tb_status_str(int status) {
+    switch (status) {
+        case TB_OK: return "ok";
+        case TB_EINVAL: return "invalid argument";
+        case TB_EDOMAIN: return "circuit outside the supported domain";
+        case TB_ENOMEM: return "insufficient memory";
+        case TB_ECUDA: return "CUDA error";
+        case TB_ETIMEOUT: return "device wait timed out";
+        default: return "unknown status";
+    }
+}
+
+const char* tb_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

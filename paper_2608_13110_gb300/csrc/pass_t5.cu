@@ -1,0 +1,6 @@
+// Pass kernels of shape P_BOT_END for window sizes 5..10 (see pass_kernel.cuh).
+#include "pass_kernel.cuh"
+
+namespace tb {
+TB_DEFINE_LAUNCH_PASS(P_BOT_END, launch_pass_t5)
+}  // namespace tb

@@ -1,0 +1,127 @@
+// Internal definitions shared by the host planner and the CUDA kernels of
+// the temporal-boundary sweep (arXiv 2608.13110, Sec. 3.1, Algorithm 1).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace tb {
+
+// Boundary passes work on tiles of 2^TILE_BITS complex64 entries (64 KB):
+// the window's address bits plus enough low address bits for coalescing.
+constexpr int TILE_BITS = 13;
+constexpr int TILE = 1 << TILE_BITS;
+constexpr int PASS_THREADS = 256;     // 8 warps, 32 entries per thread
+constexpr int REG_BITS = 5;           // entries per thread = 2^REG_BITS
+constexpr int MIN_WINDOW = 5;
+constexpr int MAX_WINDOW = 10;
+// Boundaries of width <= SMALL_H_MAX live in one CTA's shared memory for the
+// whole sweep (one CTA per bitstring).
+constexpr int SMALL_H_MAX = 12;
+constexpr int SMALL_THREADS = 256;
+constexpr int MAX_H = 33;        // widest boundary the device path evaluates
+constexpr int MAX_PLAN_H = 40;   // widest circuit the planner accepts (counters only beyond MAX_H)
+
+// Split of the boundary address bits used by the row-0 writer and the last
+// row reduction: k low bits (table), m middle bits (table), top bits.
+constexpr int LOW_BITS = 12;
+constexpr int MID_BITS = 10;
+
+// Pass shapes. A pass applies the steps of one window of address bits
+// [lo, lo+M-1] (window-relative bit w <-> address bit lo+w):
+//   FWD       forward row, targets w = 1..M-1, control w-1
+//   REV       reversed row, targets w = M-2..0, control w+1
+//   TOP       row turn at the top: FWD targets, then the next (reversed)
+//             row's targets w = M-1 (no control), M-2..0 (control w+1)
+//   BOT       row turn at address bit 0: REV targets w = M-2..0, then the
+//             next (forward) row's w = 0 (no control), 1..M-1 (control w-1)
+//   BOT_START first window of the first absorbed row: w = 0 (no control), 1..M-1
+//   BOT_END   last window of a reversed last row: w = M-2..0
+//   TOP_END   last window of a forward last row: w = 1..M-1
+enum PassType : int {
+    P_FWD = 0,
+    P_REV = 1,
+    P_TOP = 2,
+    P_BOT = 3,
+    P_BOT_START = 4,
+    P_BOT_END = 5,
+    P_TOP_END = 6,
+    P_NTYPES = 7
+};
+
+__host__ __device__ constexpr int pass_nsteps(int type, int M) {
+    return type == P_TOP || type == P_BOT ? 2 * M - 1 : type == P_BOT_START ? M : M - 1;
+}
+
+// One paired step: out[.., c, a', ..] = sum_s G[c][a'][s] in[.., c, s, ..] on
+// the target bit, c the control bit (ignored for uncontrolled steps). Two
+// variants: the step may depend on the output bit x_q of its row.
+struct StepG {
+    float2 g[2][8];  // [x variant][c*4 + a'*2 + s]
+};
+
+// Host-side description of one pass (launch arguments).
+struct PassDesc {
+    int type;
+    int M;
+    int lo;        // address bit of window bit 0
+    int step0;     // first step in the device step array
+    int nsteps;
+    int xs_step[2];  // index within the pass of a bitstring-dependent step, -1 if none
+    int xs_q[2];     // the qubit whose output bit selects its variant
+};
+
+// Byte offsets of the device tables inside the workspace head.
+struct TableLayout {
+    int64_t steps;     // StepG[n_steps]
+    int64_t step_tgt;  // int8 target bit per step
+    int64_t step_ctl;  // int8 control bit per step (-1: none)
+    int64_t step_xq;   // int16 qubit of the bitstring dependence (-1: none)
+    int64_t row_end;   // int32 index one past the last step of each absorbed row
+    int64_t init_low;  // float2[2^k]          row 0: low-bit product
+    int64_t init_mid;  // float2[2][2^m]       row 0: middle factor by bit k-1
+    int64_t init_top;  // float2[2][2][2^top]  row 0: [x][bit k+m-1][top bits]
+    int64_t red_low;   // float2[2^k][2]       last row: column vectors
+    int64_t red_mid;   // float2[2^m][4]       last row: 2x2 matrices
+    int64_t red_top;   // float2[2][2^top][2]  last row: [x] row vectors
+    int64_t total;
+};
+
+// Per-bitstring rescaling state: slot 0 is written by the row-0 writer, slot
+// k+1 by pass k, slot P+1 by the last-row reduction.
+//   maxs[slot]: float bits of max(|re|, |im|) over the boundary after it
+//   exps[slot]: the power of two the producer multiplied its input by
+struct ScaleLayout {
+    int nslots;
+    int64_t bytes_per_b;  // maxs (uint32) then exps (int32), padded
+};
+
+constexpr int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace tb
+
+namespace tb {
+
+// Window-relative target bit t and control bit c (-1: none) of step i of a
+// pass of the given shape; the planner emits steps in exactly this order.
+struct StepSpec {
+    int t;
+    int c;
+};
+
+__host__ __device__ constexpr StepSpec step_spec(int type, int M, int i) {
+    if (type == P_FWD || type == P_TOP_END) return StepSpec{i + 1, i};
+    if (type == P_REV || type == P_BOT_END) return StepSpec{M - 2 - i, M - 1 - i};
+    if (type == P_BOT_START) return StepSpec{i, i == 0 ? -1 : i - 1};
+    if (type == P_TOP) {
+        if (i < M - 1) return StepSpec{i + 1, i};
+        const int j = i - (M - 1);
+        return StepSpec{M - 1 - j, j == 0 ? -1 : M - j};
+    }
+    // P_BOT
+    if (i < M - 1) return StepSpec{M - 2 - i, M - 1 - i};
+    const int j = i - (M - 1);
+    return StepSpec{j, j == 0 ? -1 : j - 1};
+}
+
+}  // namespace tb

@@ -1,0 +1,50 @@
+// Host-side plan object of the temporal-boundary sweep.
+#pragma once
+
+#include <complex>
+#include <string>
+#include <vector>
+
+#include "tb_internal.h"
+#include "tbsweep.h"
+
+namespace tb {
+
+struct M2 {
+    std::complex<double> a[4];  // row-major 2x2
+};
+
+M2 m2_mul(const M2& A, const M2& B);
+M2 clifford(int k);
+
+struct Plan {
+    int n = 0, d = 0, h = 0;
+    tb_opts opts{};
+    std::vector<M2> U;  // (d+1)*n folded slot gates, index t*n + q
+    // paired steps of rows 1..n-2 in execution order
+    std::vector<StepG> steps;
+    std::vector<int8_t> step_tgt, step_ctl;
+    std::vector<int16_t> step_xq;
+    std::vector<int32_t> row_end;
+    // pass schedule (empty when the boundary fits one CTA)
+    std::vector<PassDesc> passes;
+    std::vector<int> windows;
+    // row-0 and last-row tables
+    int k = 0, m = 0, top = 0;
+    std::vector<float2> init_low, init_mid, init_top, red_low, red_mid, red_top;
+    // Algorithm 1 counters
+    int width = 0;
+    double log2cost = 0;
+    // device image of the tables
+    TableLayout lay{};
+    std::vector<uint8_t> blob;
+};
+
+int plan_build(Plan& P, int n, int d, const uint8_t* cliff, const uint8_t* tmask,
+               const tb_gate1q* extra, int n_extra, const tb_opts* opts, std::string& err);
+
+}  // namespace tb
+
+struct tb_plan {
+    tb::Plan p;
+};

@@ -1,0 +1,167 @@
+"""Host-side checks of the C-ABI library: it loads, exports every declared
+symbol, and its planner reproduces the numbers the paper prints. No CUDA call
+is made (the planner is host-only), so these run without a GPU."""
+import json
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+GOLDEN = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_numbers.json")))
+
+
+@pytest.fixture(scope="module")
+def tb():
+    from paper_2608_13110_gb300 import build as b
+    b.build()
+    import paper_2608_13110_gb300 as mod
+    return mod
+
+
+def test_library_exports_every_declared_symbol(tb):
+    header = open(os.path.join(ROOT, "include", "tbsweep.h")).read()
+    declared = set(re.findall(r"TB_API\s+[\w\s\*]+?\b(tb_\w+)\s*\(", header))
+    assert len(declared) >= 12
+    for name in declared:
+        assert hasattr(tb._lib, name), name
+    assert declared == set(tb.EXPORTED)
+
+
+def test_clifford_table_matches_oracle(tb, oracle_mod):
+    ref = oracle_mod.clifford_table()
+    for k in range(24):
+        np.testing.assert_allclose(tb.clifford_matrix(k), ref[k], atol=1e-15)
+
+
+def test_width_and_cost_at_n70_d70(tb):
+    g = GOLDEN["width_cost_open_chi2_n70_d70"]
+    info = tb.Plan(g["n"], g["d"]).info
+    assert info["width"] == g["W"]
+    assert abs(info["log2_cost"] - g["log2_C"]) < g["log2_C_tolerance"]
+
+
+def test_constructive_width_is_ceil_d_over_2(tb):
+    g = GOLDEN["constructive_width"]
+    for d in g["d"]:
+        assert tb.Plan(g["n"], d).info["width"] == math.ceil(d / 2), d
+    for n, d in [(12, 8), (30, 40), (32, 48), (70, 56), (70, 64), (20, 16), (40, 48)]:
+        info = tb.Plan(n, d).info
+        assert info["width"] == d // 2 == info["boundary_bits"]
+
+
+def test_boundary_payload_bytes(tb):
+    g = GOLDEN["boundary_payload_bytes"]
+    assert tb.Plan(70, 70).info["boundary_bytes"] == g["d70_complex64"]
+    assert tb.Plan(70, 60).info["boundary_bytes"] == g["d60_complex64"]
+
+
+def test_cz_counts_of_the_brickwork_convention():
+    g = GOLDEN["cz_counts_n70"]
+    n = g["n"]
+    per_layer = [len(range(l % 2, n - 1, 2)) for l in range(70)]
+    assert sorted(set(per_layer)) == g["per_layer"]
+    assert sum(per_layer) == g["total_d70"]
+
+
+def test_plan_topology_independent_of_gate_values(tb):
+    """Width, cost, step and pass counts do not depend on the one-qubit gates
+    or on the number and placement of T gates (Sec. 1 contributions, Sec. 3.1)."""
+    c = W.precision_70_64(nb=1)
+    a = tb.Plan.from_circuit(c).info
+    b = tb.Plan.from_circuit(c.clifford_twin()).info
+    e = tb.Plan(70, 64).info
+    for k in ("width", "log2_cost", "n_steps", "n_passes", "boundary_bytes", "table_bytes"):
+        assert a[k] == b[k] == e[k], k
+
+
+def test_step_and_pass_counts(tb):
+    for n, d in [(70, 64), (70, 56), (30, 40), (12, 8), (2, 30), (3, 26)]:
+        info = tb.Plan(n, d).info
+        h = d // 2
+        assert info["n_steps"] == max(0, n - 2) * h
+        if h <= 12 or n == 2:
+            assert info["n_passes"] == 0
+        else:
+            # every pass advances at most 2*MAX_WINDOW-1 steps
+            assert info["n_passes"] >= info["n_steps"] / 19
+    # n=70, d=64 with 10-bit windows: 3 passes per absorbed row plus the first window
+    assert tb.Plan(70, 64).info["n_passes"] <= 68 * 3 + 1
+
+
+def test_window_options(tb):
+    for wb, bb, tt in [(10, 10, 10), (8, 0, 0), (5, 0, 0), (6, 9, 9), (9, 0, 7)]:
+        info = tb.Plan(40, 60, window_bits=wb, bottom_bits=bb, top_bits=tt).info
+        assert info["n_passes"] > 0
+    with pytest.raises(tb.TbError):
+        tb.Plan(40, 60, window_bits=11)
+    with pytest.raises(tb.TbError):
+        tb.Plan(40, 60, window_bits=4)
+
+
+@pytest.mark.parametrize("n,d", [(1, 8), (10, 7), (10, 0), (10, 82), (0, 4)])
+def test_domain_errors(tb, n, d):
+    with pytest.raises(tb.TbError) as e:
+        tb.Plan(n, d)
+    assert e.value.status == tb.TB_EDOMAIN
+
+
+def test_argument_errors(tb):
+    n, d = 6, 8
+    cl = np.zeros((d + 1, n), np.uint8)
+    cl[3, 2] = 24
+    with pytest.raises(tb.TbError) as e:
+        tb.Plan(n, d, cl)
+    assert e.value.status == tb.TB_EINVAL
+    tm = np.zeros((d, n), np.uint8)
+    tm[1, 1] = 2
+    with pytest.raises(tb.TbError) as e:
+        tb.Plan(n, d, None, tm)
+    assert e.value.status == tb.TB_EINVAL
+    with pytest.raises(tb.TbError) as e:
+        tb.Plan(n, d, extra=[(n, 0, np.eye(2))])
+    assert e.value.status == tb.TB_EINVAL
+
+
+def test_bits_are_checked_before_any_device_work(tb):
+    """tb_amplitudes rejects a bitstring entry outside {0,1} on the host."""
+    import ctypes
+    plan = tb.Plan(6, 8)
+    bits = np.zeros((2, 6), np.uint8)
+    bits[1, 3] = 2
+    out = np.empty(4, np.float64)
+    rc = tb._lib.tb_amplitudes(plan.handle, bits.ctypes.data_as(tb._u8p), 2, ctypes.c_void_p(256),
+                               1 << 30, out.ctypes.data_as(tb._dp), None)
+    assert rc == tb.TB_EINVAL
+
+
+def test_workspace_sizes(tb):
+    plan = tb.Plan(70, 64)
+    one = plan.workspace_bytes(1)
+    assert one >= (8 << 32)
+    assert plan.workspace_min_bytes() >= (8 << 32)
+    assert plan.workspace_bytes(16) >= one
+    small = tb.Plan(12, 8)
+    assert small.workspace_bytes(64) < (1 << 20)
+
+
+def test_log_xeb_matches_oracle(tb, oracle_mod):
+    rng = np.random.default_rng(2)
+    amps = (rng.standard_normal(50) + 1j * rng.standard_normal(50)) * 1e-5
+    assert abs(tb.log_xeb(amps, 30) - oracle_mod.log_xeb(amps, 30)) < 1e-12
+
+
+def test_pass_cases_cover_every_shape(tb):
+    """The GPU parity cases exercise every pass shape with every window size."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("gpu_parity", os.path.join(ROOT, "tests", "test_gpu_parity.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    seen = set()
+    for n, d, wb, bb, tt in mod.PASS_CASES:
+        seen |= {(s, m) for s, m, _ in tb.Plan(n, d, window_bits=wb, bottom_bits=bb, top_bits=tt).schedule}
+    assert seen == {(s, m) for s in tb.Plan.PASS_SHAPES for m in range(5, 11)}
