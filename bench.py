@@ -1,0 +1,315 @@
+"""Benchmark: exact amplitudes of the n=70, d=64 brickwork workload (width 32,
+32 GiB complex64 boundary, 426 T gates, 16 uniform bitstrings per step) on
+one GB300 per rank.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+A step is one batch of 16 amplitudes through the whole sweep (row-0 writer,
+every boundary pass, last-row reduction). ``value`` is amplitudes per second
+with the bitstrings already in HBM (device API); ``e2e`` is the same metric
+through the host API, including the table upload, the host->device copy of the
+bitstrings from pinned memory and the device->host copy of the amplitudes.
+Multi-GPU runs are independent replicas (each rank its own bitstrings; no
+collective on the data path): weak scaling, value = all ranks' amplitudes /
+the slowest rank's time.
+
+``--impl reference`` times the FP64 CPU oracle (the naive row-by-row network
+contraction) on the host cores instead, on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "amplitudes/s (n=70, d=64 brickwork, width 32)"
+UNIT = "amps/s"
+WORKLOAD = "brickwork CZ n=70 d=64, random Cliffords, 426 T, 16 uniform bitstrings/step, width 32 (32 GiB c64 boundary)"
+CPU_SAMPLE = (30, 40)  # oracle-sized slice with the same gate statistics
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def dist_setup(backend_pref):
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend_pref, rank=rank, world_size=world)
+    return rank, world, local
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """Largest value of x over all ranks (host scalar)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int, device=None):
+    if world > 1:
+        import torch.distributed as dist
+        if device is not None and device.type == "cuda":
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+# --------------------------------------------------------------------- clocks
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, gpu_index: int):
+        self.p = None
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={CLOCK_FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(gpu_index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=10)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, smax, power = [], [], []
+        names = ("active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        seen = set()
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names[1:], f[5:9]):
+                if v.lower().startswith("active"):
+                    seen.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(seen)}
+
+
+# ------------------------------------------------------------ CPU baseline
+def cpu_baseline(seconds_cap: float = 30.0) -> dict:
+    """FP64 oracle (naive row-by-row contraction) on the n=30, d=40 slice with
+    the workload's gate statistics, scaled to the n=70, d=64 workload by the
+    ratio of Algorithm 1's contraction costs of the two circuits."""
+    import oracle
+    import paper_2608_13110_gb300 as tb
+    c = W.random_circuit(CPU_SAMPLE[0], CPU_SAMPLE[1], None, 4, 777)
+    u = oracle.circuit_gates(c)
+    done = 0
+    t0 = time.perf_counter()
+    while done < c.bits.shape[0]:
+        oracle.nb_amplitudes(c.n, c.d, u, c.bits[done:done + 1])
+        done += 1
+        if time.perf_counter() - t0 > seconds_cap / 2:
+            break
+    dt = time.perf_counter() - t0
+    slice_rate = done / dt
+    ratio = 2.0 ** (tb.Plan(70, 64).info["log2_cost"] - tb.Plan(*CPU_SAMPLE).info["log2_cost"])
+    return {"value": slice_rate / ratio, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": (f"{done} amplitude(s) of an n={CPU_SAMPLE[0]}, d={CPU_SAMPLE[1]} slice (width 20) "
+                       f"in {dt:.1f} s = {slice_rate:.3g} amps/s, divided by the Algorithm 1 cost ratio "
+                       f"C(70,64)/C(30,40) = {ratio:.4g}")}
+
+
+# --------------------------------------------------------------------- traffic
+def pass_traffic(h: int):
+    """DRAM bytes per pass launch from the committed ncu summary, scaled to a
+    2^h boundary, or None if absent or taken on other kernel sources."""
+    path = os.path.join(ROOT, "profiles", "pass_kernel_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    import hashlib
+    src = os.path.join(ROOT, "paper_2608_13110_gb300", "csrc", "pass_kernel.cuh")
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    kv = {}
+    for line in open(path):
+        if "=" in line and not line.lstrip().startswith("#"):
+            k, v = line.split("=", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("pass_kernel_sha256_16") != digest:
+        return None
+    try:
+        return float(kv["dram_bytes_per_entry"]) * float(2 ** h)
+    except (KeyError, ValueError):
+        return None
+
+
+# --------------------------------------------------------------------- arms
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    steps, warm = args.steps, args.warmup
+    per_step = max(2.0, min(20.0, 150.0 / max(1, steps + warm)))
+    for _ in range(warm):
+        cpu_baseline(per_step)
+    vals = [cpu_baseline(per_step) for _ in range(steps)]
+    v = statistics.median(x["value"] for x in vals)
+    cb = dict(vals[-1])
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": steps, "warmup": warm, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "complex128", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": 70, "d": 64, "n_t": 426, "bitstrings_per_step": 16,
+                       "parallelism": "replicas"},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    import paper_2608_13110_gb300 as tb
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    nb = args.nb
+    c = W.precision_70_64(replica=rank, nb=nb)
+    plan = tb.Plan.from_circuit(c)
+    info = plan.info
+    h = info["boundary_bits"]
+    ws = torch.empty(plan.workspace_bytes(nb), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    plan.upload(ws, stream)
+    d_bits = torch.from_numpy(c.bits).to(dev)
+    d_out = torch.empty((nb, 2), dtype=torch.float64, device=dev)
+
+    def step():
+        plan.amplitudes_device(d_bits, ws, d_out, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    barrier(world, dev)
+    torch.cuda.synchronize(dev)
+
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    tb.profile_begin()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    prof = tb.profile_end()
+    clk = clocks.stop()
+    t_dev = e0.elapsed_time(e1) / 1e3
+    amps = d_out.cpu().numpy().view(np.complex128).reshape(-1)
+
+    barrier(world, dev)
+    # end to end through the host API: pinned host bitstrings in, amplitudes out
+    bits_pin = torch.from_numpy(c.bits).pin_memory()
+    out_pin = torch.empty((nb, 2), dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        plan.amplitudes(bits_pin.numpy(), ws=ws, stream=stream, out=out_pin.numpy())
+    t_e2e = (time.perf_counter() - t0)
+    e2e_amps = out_pin.numpy().view(np.complex128).reshape(-1)
+
+    t_dev_max = max_over_ranks(t_dev, world, dev)
+    t_e2e_max = max_over_ranks(t_e2e, world, dev)
+    value = world * nb * args.steps / t_dev_max
+    e2e_value = world * nb * args.e2e_steps / t_e2e_max
+
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = json.load(open(pk))
+    hbm_peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm_peak else "fallback"
+    hbm_peak = hbm_peak or 6800.0
+    p = prof["pass"]
+    achieved = p["bytes"] / (p["ms"] / 1e3) / 1e9 if p["ms"] > 0 else None
+    n_launch = sum(v["launches"] for v in prof.values())
+    traffic = pass_traffic(h)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_dev_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "complex64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": 70, "d": 64, "n_t": 426, "bitstrings_per_step": nb,
+                   "width": info["width"], "passes_per_amplitude": info["n_passes"],
+                   "l2": "inputs larger than L2 (32 GiB boundary, 129 MB L2)",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(c.bits.nbytes + info["table_bytes"]),
+                "d2h_bytes_per_step": int(16 * nb)},
+        "gpu_launches": n_launch,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": (achieved / hbm_peak) if achieved else None, "traffic": traffic,
+                     "kernel": "pass_kernel", "peak_source": f"{peak_src} copy bandwidth",
+                     "pass_launches": p["launches"], "pass_ms_total": p["ms"],
+                     "pass_share_of_kernel_time": p["ms"] / max(1e-9, sum(v["ms"] for v in prof.values()))},
+        "clocks": clk,
+        "sanity": {"log_xeb": tb.log_xeb(amps, 70), "e2e_matches_device": bool(np.array_equal(amps, e2e_amps))},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--nb", type=int, default=16)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        rank, world, _ = dist_setup("gloo")
+        run_reference(args, rank, world)
+    else:
+        rank, world, local = dist_setup("nccl")
+        run_ours(args, rank, world, local)
+    if _env_int("WORLD_SIZE", 1) > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -155,6 +155,24 @@ TB_API int tb_amplitudes(const tb_plan* plan, const uint8_t* bits, int64_t nb, v
  * or -1 for a NULL plan. */
 TB_API int tb_plan_schedule(const tb_plan* plan, int32_t* sched, int cap);
 
+/* Kernel timing (tracing aid). While enabled, every kernel this library
+ * launches is bracketed by CUDA events on its stream. Classes: 0 boundary
+ * passes, 1 row-0 writer, 2 last-row reduction, 3 finalisation, 4 narrow
+ * (whole boundary in shared memory). bytes[c] is the algorithmic HBM traffic
+ * of those launches: a pass reads and writes every boundary entry once
+ * (16 bytes per entry), the writer writes 8, the reduction reads 8. */
+typedef struct {
+    int64_t launches[5];
+    double ms[5];
+    double bytes[5];
+} tb_profile_t;
+
+/* Start recording (clears earlier records). Process-wide; not reentrant. */
+TB_API int tb_profile_begin(void);
+
+/* Stop recording, wait for the recorded events and sum them into *out. */
+TB_API int tb_profile_end(tb_profile_t* out);
+
 /* log-XEB estimator F = gamma + n ln 2 + (1/N) sum_i ln |amp_i|^2 (Sec. 5.2,
  * normalized log-XEB equation), host FP64. amp: 2*nb doubles (re, im).
  * A zero amplitude gives -inf. */

@@ -54,6 +54,8 @@ _sig = {
     "tb_amplitudes_device": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _vp, ctypes.c_int64, _vp, _vp]),
     "tb_amplitudes": (ctypes.c_int, [_vp, _u8p, ctypes.c_int64, _vp, ctypes.c_int64, _dp, _vp]),
     "tb_plan_schedule": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int32), ctypes.c_int]),
+    "tb_profile_begin": (ctypes.c_int, []),
+    "tb_profile_end": (ctypes.c_int, [ctypes.c_void_p]),
     "tb_log_xeb": (ctypes.c_int, [_dp, ctypes.c_int64, ctypes.c_int, _dp]),
     "tb_clifford_matrix": (ctypes.c_int, [ctypes.c_int, _dp]),
     "tb_plan_destroy": (None, [_vp]),
@@ -214,6 +216,28 @@ class Plan:
         _check(_lib.tb_amplitudes(self._h, b.ctypes.data_as(_u8p), nb, ws.data_ptr(), ws.numel(),
                                   out.ctypes.data_as(_dp), _stream_handle(stream)), "tb_amplitudes")
         return out.view(np.complex128).reshape(-1)
+
+
+class _Profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64 * 5), ("ms", ctypes.c_double * 5),
+                ("bytes", ctypes.c_double * 5)]
+
+
+PROFILE_CLASSES = ("pass", "init", "reduce", "finalize", "narrow")
+
+
+def profile_begin() -> None:
+    """Bracket every kernel launch with CUDA events from now on."""
+    _check(_lib.tb_profile_begin(), "tb_profile_begin")
+
+
+def profile_end() -> dict:
+    """Stop recording; {class: {"launches", "ms", "bytes"}} for the launches
+    recorded since profile_begin()."""
+    p = _Profile()
+    _check(_lib.tb_profile_end(ctypes.byref(p)), "tb_profile_end")
+    return {c: {"launches": int(p.launches[i]), "ms": float(p.ms[i]), "bytes": float(p.bytes[i])}
+            for i, c in enumerate(PROFILE_CLASSES)}
 
 
 def log_xeb(amps, n: int) -> float:

@@ -11,6 +11,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "misc_kernels.cuh"
 #include "pass_kernel.cuh"
@@ -34,6 +35,50 @@ int fail(int code, const std::string& msg) {
     } while (0)
 
 using namespace tb;
+
+// ---- optional per-launch timing -------------------------------------------
+enum { PC_PASS = 0, PC_INIT = 1, PC_REDUCE = 2, PC_FINAL = 3, PC_SMALL = 4, PC_N = 5 };
+
+struct Profiler {
+    std::mutex mu;
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    struct Rec { int cls; double bytes; size_t e0, e1; };
+    std::vector<Rec> recs;
+    size_t used = 0;
+
+    cudaEvent_t take(size_t& idx) {
+        if (used == pool.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            pool.push_back(e);
+        }
+        idx = used;
+        return pool[used++];
+    }
+};
+Profiler g_prof;
+
+// Bracket one launch with events when profiling is on.
+struct ProfScope {
+    bool active = false;
+    size_t i0 = 0, i1 = 0;
+    int cls;
+    double bytes;
+    cudaStream_t st;
+    ProfScope(int c, double b, cudaStream_t s) : cls(c), bytes(b), st(s) {
+        std::lock_guard<std::mutex> lk(g_prof.mu);
+        if (!g_prof.on) return;
+        cudaEvent_t e = g_prof.take(i0);
+        if (e && cudaEventRecord(e, st) == cudaSuccess) active = true;
+    }
+    ~ProfScope() {
+        if (!active) return;
+        std::lock_guard<std::mutex> lk(g_prof.mu);
+        cudaEvent_t e = g_prof.take(i1);
+        if (e && cudaEventRecord(e, st) == cudaSuccess) g_prof.recs.push_back({cls, bytes, i0, i1});
+    }
+};
 
 constexpr int64_t DEFAULT_BATCH_ENTRIES = (int64_t)1 << 30;  // 8 GiB of boundaries
 
@@ -125,6 +170,7 @@ int run_device(const Plan& P, const uint8_t* d_bits, int64_t nb, void* d_ws, int
             sp.nb = (int)std::min(chunk, nb - b0);
             sp.bits = d_bits + b0 * P.n;
             sp.out = d_out + 2 * b0;
+            ProfScope ps(PC_SMALL, 0.0, st);
             TB_CUDA(launch_small(sp, st));
         }
         return TB_OK;
@@ -164,7 +210,10 @@ int run_device(const Plan& P, const uint8_t* d_bits, int64_t nb, void* d_ws, int
         ip.topt = tab<float2>(d_ws, L.init_top);
         ip.maxs = maxs;
         ip.sstride = sstride;
-        TB_CUDA(launch_init(ip, (int)std::min<int64_t>(ip.nchunks, 8LL * nsm), st));
+        {
+            ProfScope ps(PC_INIT, 8.0 * (double)nbat * (double)b_stride, st);
+            TB_CUDA(launch_init(ip, (int)std::min<int64_t>(ip.nchunks, 8LL * nsm), st));
+        }
 
         for (size_t k = 0; k < P.passes.size(); ++k) {
             const PassDesc& d = P.passes[k];
@@ -183,6 +232,7 @@ int run_device(const Plan& P, const uint8_t* d_bits, int64_t nb, void* d_ws, int
             pp.sstride = sstride;
             pp.slot = (int)k;
             const int grid = (int)std::min<int64_t>(pp.ntiles, nsm);  // one persistent CTA per SM
+            ProfScope ps(PC_PASS, 16.0 * (double)nbat * (double)b_stride, st);
             TB_CUDA(launch_pass(d, pp, grid, st));
         }
 
@@ -202,7 +252,10 @@ int run_device(const Plan& P, const uint8_t* d_bits, int64_t nb, void* d_ws, int
         rp.sstride = sstride;
         rp.slot = (int)P.passes.size();
         rp.partials = partials;
-        TB_CUDA(launch_reduce(rp, st));
+        {
+            ProfScope ps(PC_REDUCE, 8.0 * (double)nbat * (double)b_stride, st);
+            TB_CUDA(launch_reduce(rp, st));
+        }
 
         FinalizeParams fp;
         fp.partials = partials;
@@ -212,7 +265,10 @@ int run_device(const Plan& P, const uint8_t* d_bits, int64_t nb, void* d_ws, int
         fp.nslots = c.nslots;
         fp.nbatch = nbat;
         fp.out = d_out + 2 * b0;
-        TB_CUDA(launch_finalize(fp, st));
+        {
+            ProfScope ps(PC_FINAL, 0.0, st);
+            TB_CUDA(launch_finalize(fp, st));
+        }
     }
     return TB_OK;
 }
@@ -328,6 +384,32 @@ int tb_amplitudes(const tb_plan* plan, const uint8_t* bits, int64_t nb, void* d_
     if (rc != TB_OK) return rc;
     TB_CUDA(cudaMemcpyAsync(out, d_out, (size_t)(16 * nb), cudaMemcpyDeviceToHost, st));
     TB_CUDA(cudaStreamSynchronize(st));
+    return TB_OK;
+}
+
+int tb_profile_begin(void) {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    g_prof.on = true;
+    g_prof.recs.clear();
+    g_prof.used = 0;
+    return TB_OK;
+}
+
+int tb_profile_end(tb_profile_t* out) {
+    if (!out) return fail(TB_EINVAL, "out is NULL");
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    g_prof.on = false;
+    std::memset(out, 0, sizeof(*out));
+    for (const auto& r : g_prof.recs) {
+        TB_CUDA(cudaEventSynchronize(g_prof.pool[r.e1]));
+        float ms = 0.0f;
+        TB_CUDA(cudaEventElapsedTime(&ms, g_prof.pool[r.e0], g_prof.pool[r.e1]));
+        out->launches[r.cls] += 1;
+        out->ms[r.cls] += ms;
+        out->bytes[r.cls] += r.bytes;
+    }
+    g_prof.recs.clear();
+    g_prof.used = 0;
     return TB_OK;
 }
 
