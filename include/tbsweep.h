@@ -173,7 +173,7 @@ TB_API int tb_profile_begin(void);
 /* Stop recording, wait for the recorded events and sum them into *out. */
 TB_API int tb_profile_end(tb_profile_t* out);
 
-/* log-XEB estimator F = gamma + n ln 2 + (1/N) sum_i ln |amp_i|^2 (Sec. 5.2,
+/* log-XEB estimator/* log-XEB estimator F = gamma + n ln 2 + (1/N) sum_i ln |amp_i|^2 (Sec. 5.2,
  * normalized log-XEB equation), host FP64. amp: 2*nb doubles (re, im).
  * A zero amplitude gives -inf. */
 TB_API int tb_log_xeb(const double* amp, int64_t nb, int n, double* out);

@@ -231,7 +231,7 @@ int run_device(const Plan& P, const uint8_t* d_bits, int64_t nb, void* d_ws, int
             pp.exps = exps;
             pp.sstride = sstride;
             pp.slot = (int)k;
-            const int grid = (int)std::min<int64_t>(pp.ntiles, nsm);  // one persistent CTA per SM
+            const int grid = (int)std::min<int64_t>(pp.ntiles, (int64_t)PASS_CTAS_PER_SM * nsm);  // persistent CTAs
             ProfScope ps(PC_PASS, 16.0 * (double)nbat * (double)b_stride, st);
             TB_CUDA(launch_pass(d, pp, grid, st));
         }

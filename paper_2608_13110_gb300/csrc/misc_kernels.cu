@@ -115,10 +115,22 @@ __global__ void __launch_bounds__(REDUCE_THREADS) reduce_kernel(const ReducePara
         const float2 r1 = cfma(tv[1], md[3], cmul(tv[0], md[1]));
         const float2* src = p.B + (int64_t)b * p.b_stride + (c << p.k);
         float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
-        for (int e = threadIdx.x; e < nk; e += blockDim.x) {
-            const float2 v = src[e];
-            a0 = cfma(v, slow[2 * e], a0);
-            a1 = cfma(v, slow[2 * e + 1], a1);
+        // 16 independent loads in flight per thread, then the products
+        for (int e0 = threadIdx.x; e0 < nk; e0 += 16 * REDUCE_THREADS) {
+            float2 v[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int e = e0 + i * REDUCE_THREADS;
+                v[i] = e < nk ? __ldcs(src + e) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int e = e0 + i * REDUCE_THREADS;
+                if (e < nk) {
+                    a0 = cfma(v[i], slow[2 * e], a0);
+                    a1 = cfma(v[i], slow[2 * e + 1], a1);
+                }
+            }
         }
         const float2 cv = cfma(r1, a1, cmul(r0, a0));
         ar += (double)cv.x;

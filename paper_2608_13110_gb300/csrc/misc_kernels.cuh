@@ -66,7 +66,7 @@ struct SmallParams {
 };
 
 constexpr int REDUCE_THREADS = 256;
-constexpr int MAX_RED_BLOCKS = 256;
+constexpr int MAX_RED_BLOCKS = 1024;
 
 cudaError_t launch_init(const InitParams& p, int grid, cudaStream_t st);
 cudaError_t launch_reduce(const ReduceParams& p, cudaStream_t st);

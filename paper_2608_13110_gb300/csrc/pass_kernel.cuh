@@ -7,11 +7,11 @@
 // A pass applies a compile-time sequence of controlled 2x2 steps to every
 // tile of 2^13 complex64 entries: the window's M address bits plus 13-M low
 // address bits (the 13 lowest bits when the window starts at bit 0). Each of
-// the 256 threads holds 32 entries in registers. A step acts on a 5-bit
-// "register run" of the tile; between runs the tile is transposed through
-// shared memory (XOR-swizzled, conflict-free for every run base 0..8). The
-// first and last run keep 8 or more consecutive entries on consecutive lanes,
-// so loads and stores go straight between HBM and registers.
+// the 256 threads holds 32 entries; one CTA per SM. A step acts on a
+// 5-bit "register run" of the tile; between runs the tile is re-read from
+// shared memory (XOR-swizzled, conflict-free for every run base used). Tiles
+// stream in through a 3-stage cp.async ring; stores go from registers
+// straight to HBM with 8 or more consecutive entries on consecutive lanes.
 //
 // Rescaling: the producer of this pass's input left max(|re|,|im|) of its
 // output in maxs[slot]; this pass multiplies its input by 2^s (exact; folded
@@ -67,7 +67,7 @@ struct Shape {
     }
     static constexpr int last_run() { return BOT ? RB : run_of(NS - 1); }
     static constexpr bool valid() {
-        if (M < MIN_WINDOW || M > MAX_WINDOW) return false;
+        if (M < MIN_WINDOW || M > (BOT ? MAX_WINDOW : MAX_WINDOW_HIGH)) return false;
         for (int j = 0; j < NS; ++j)
             if (!in_run(C + step_spec(TYPE, M, j).t, run_of(j))) return false;
         return true;
@@ -90,135 +90,247 @@ __device__ __forceinline__ uint32_t swz(uint32_t idx) {
     return idx ^ (((idx >> 6) & 1u) << 1) ^ (((idx >> 7) & 1u) << 2) ^ ((((idx >> 5) ^ (idx >> 8)) & 1u) << 3);
 }
 
-// a*g0 + b*g1 in complex arithmetic.
-__device__ __forceinline__ float2 cmac2(float2 g0, float2 a, float2 g1, float2 b) {
-    float2 r;
-    r.x = fmaf(g0.x, a.x, fmaf(-g0.y, a.y, fmaf(g1.x, b.x, -g1.y * b.y)));
-    r.y = fmaf(g0.x, a.y, fmaf(g0.y, a.x, fmaf(g1.x, b.y, g1.y * b.x)));
-    return r;
+
+// ---------------------------------------------------------------------------
+// Packed complex arithmetic. A thread's 32 entries of register run R are
+// j = k + 16 v (k: run bits 0..3, v: run bit 4). They are held "planar" in
+// packed pairs P[k] = (re_k, re_(k+16)), Q[k] = (im_k, im_(k+16)), so that
+// one __ffma2_rn (sm_100+ paired FP32 FMA) advances two entries that share
+// their coefficient. A step on run bit K < 4 with coefficients shared by both
+// lanes needs 8 paired FMAs per pair of packed registers (half the scalar
+// count); a step whose control is run bit 4 uses lane-split coefficients; a
+// step whose target is run bit 4 mixes the two lanes of one packed register.
+//
+// Coefficients are staged in shared memory already packed, 24 float2 per
+// (step, bitstring variant):
+//   KIND_F  (target, control < 4 or none): for c in 0,1:
+//           [g00r g00i -g00i g01r g01i -g01i g10r g10i -g10i g11r g11i -g11i],
+//           each broadcast to both lanes
+//   KIND_VC (control = run bit 4): the same 12 values with lane c = control
+//   KIND_VT (target = run bit 4): for c in 0,1: [Ar Ai -Ai Br Bi -Bi],
+//           A = (g00, g11) (own lane), B = (g01, g10) (other lane)
+// ---------------------------------------------------------------------------
+constexpr int VBIT = 4;
+constexpr int KIND_F = 0, KIND_VC = 1, KIND_VT = 2;
+constexpr int CO = 24;  // packed coefficients per (step, variant)
+
+__device__ __forceinline__ float2 f2x(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 swap2(float2 a) { return make_float2(a.y, a.x); }
+
+// out = g0 * a + g1 * b (complex) on planar pairs; cf = 6 packed coefficients
+// [g0r g0i -g0i g1r g1i -g1i].
+__device__ __forceinline__ void cmac_planar(const float2* cf, float2 aP, float2 aQ, float2 bP, float2 bQ,
+                                            float2& oP, float2& oQ) {
+    oP = fma2(cf[0], aP, fma2(cf[2], aQ, fma2(cf[3], bP, mul2(cf[5], bQ))));
+    oQ = fma2(cf[0], aQ, fma2(cf[1], aP, fma2(cf[3], bQ, mul2(cf[4], bP))));
 }
 
-// G = (G[a'][s]) on register bit K, same matrix for every pair.
-template <int K>
-__device__ __forceinline__ void step_plain(float2 (&v)[32], const float2 (&g)[4]) {
+__device__ __forceinline__ void load_cf(float2 (&c)[12], const float2* src, float s) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        if (j & (1 << K)) continue;
-        const int j1 = j | (1 << K);
-        const float2 a = v[j], b = v[j1];
-        v[j] = cmac2(g[0], a, g[1], b);
-        v[j1] = cmac2(g[2], a, g[3], b);
+    for (int i = 0; i < 6; ++i) {
+        const float4 q = s4[i];
+        c[2 * i] = make_float2(q.x * s, q.y * s);
+        c[2 * i + 1] = make_float2(q.z * s, q.w * s);
     }
 }
 
-// G[c] on register bit K, control c on register bit KC.
-template <int K, int KC>
-__device__ __forceinline__ void step_ctrl(float2 (&v)[32], const float2 (&g0)[4], const float2 (&g1)[4]) {
+// Target run bit K < 4 (pairs of packed registers). CK: -1 none (block 0),
+// 0..3 control run bit (block per pair), 4 control = run bit 4 (lane split),
+// 5 external control (block chosen by the caller).
+template <int K, int CK>
+__device__ __forceinline__ void step_pairs(float2 (&P)[16], float2 (&Q)[16], const float2 (&c0)[12],
+                                           const float2 (&c1)[12]) {
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        if (j & (1 << K)) continue;
-        const int j1 = j | (1 << K);
-        const float2 a = v[j], b = v[j1];
-        if ((j >> KC) & 1) {
-            v[j] = cmac2(g1[0], a, g1[1], b);
-            v[j1] = cmac2(g1[2], a, g1[3], b);
+    for (int k = 0; k < 16; ++k) {
+        if (k & (1 << K)) continue;
+        const int k1 = k | (1 << K);
+        const bool hi = (CK >= 0 && CK < 4) ? (((k >> CK) & 1) != 0) : false;
+        float2 p0, q0, p1, q1;
+        if (hi) {
+            cmac_planar(c1, P[k], Q[k], P[k1], Q[k1], p0, q0);
+            cmac_planar(c1 + 6, P[k], Q[k], P[k1], Q[k1], p1, q1);
         } else {
-            v[j] = cmac2(g0[0], a, g0[1], b);
-            v[j1] = cmac2(g0[2], a, g0[3], b);
+            cmac_planar(c0, P[k], Q[k], P[k1], Q[k1], p0, q0);
+            cmac_planar(c0 + 6, P[k], Q[k], P[k1], Q[k1], p1, q1);
+        }
+        P[k] = p0; Q[k] = q0; P[k1] = p1; Q[k1] = q1;
+    }
+}
+
+// Target run bit 4: the pair is the two lanes of one packed register.
+template <int CK>
+__device__ __forceinline__ void step_lanes(float2 (&P)[16], float2 (&Q)[16], const float2 (&c0)[12],
+                                           const float2 (&c1)[12]) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const bool hi = (CK >= 0 && CK < 4) ? (((k >> CK) & 1) != 0) : false;
+        const float2 p = P[k], q = Q[k];
+        float2 op, oq;
+        if (hi) cmac_planar(c1, p, q, swap2(p), swap2(q), op, oq);  // [Ar Ai -Ai Br Bi -Bi]
+        else    cmac_planar(c0, p, q, swap2(p), swap2(q), op, oq);
+        P[k] = op; Q[k] = oq;
+    }
+}
+
+template <class SH>
+__host__ __device__ constexpr int step_kind(int i) {
+    const StepSpec sp = step_spec(SH::TYPE, SH::M, i);
+    const int R = SH::run_of(i);
+    const int K = SH::C + sp.t - R;
+    if (K == VBIT) return KIND_VT;
+    if (sp.c >= 0 && in_run(SH::C + sp.c, R) && SH::C + sp.c - R == VBIT) return KIND_VC;
+    return KIND_F;
+}
+
+template <class SH>
+__host__ __device__ constexpr uint64_t step_kinds() {
+    uint64_t k = 0;
+    for (int i = 0; i < SH::NS; ++i) k |= (uint64_t)step_kind<SH>(i) << (2 * i);
+    return k;
+}
+
+// Stage the packed coefficients of every step and variant into shared memory.
+template <class SH>
+__device__ __forceinline__ void stage_coefficients(const StepG* steps, float2* sc, uint32_t tid) {
+    constexpr uint64_t KINDS = step_kinds<SH>();
+    for (int w = tid; w < SH::NS * 2; w += PASS_THREADS) {
+        const int i = w >> 1, x = w & 1;
+        const float2* g = steps[i].g[x];  // [c*4 + a'*2 + s]
+        float2* o = sc + w * CO;
+        const int kind = (int)((KINDS >> (2 * i)) & 3u);
+        if (kind == KIND_F) {
+            for (int c = 0; c < 2; ++c)
+                for (int e = 0; e < 4; ++e) {
+                    const float2 z = g[c * 4 + e];
+                    o[c * 12 + 3 * e + 0] = f2x(z.x);
+                    o[c * 12 + 3 * e + 1] = f2x(z.y);
+                    o[c * 12 + 3 * e + 2] = f2x(-z.y);
+                }
+        } else if (kind == KIND_VC) {
+            for (int e = 0; e < 4; ++e) {
+                const float2 z0 = g[e], z1 = g[4 + e];
+                o[3 * e + 0] = make_float2(z0.x, z1.x);
+                o[3 * e + 1] = make_float2(z0.y, z1.y);
+                o[3 * e + 2] = make_float2(-z0.y, -z1.y);
+            }
+            for (int e = 12; e < 24; ++e) o[e] = make_float2(0.f, 0.f);
+        } else {
+            for (int c = 0; c < 2; ++c) {
+                const float2 A0 = g[c * 4 + 0], A1 = g[c * 4 + 3];  // own lane: g00 (lo), g11 (hi)
+                const float2 B0 = g[c * 4 + 1], B1 = g[c * 4 + 2];  // other lane: g01 (lo), g10 (hi)
+                o[c * 12 + 0] = make_float2(A0.x, A1.x);
+                o[c * 12 + 1] = make_float2(A0.y, A1.y);
+                o[c * 12 + 2] = make_float2(-A0.y, -A1.y);
+                o[c * 12 + 3] = make_float2(B0.x, B1.x);
+                o[c * 12 + 4] = make_float2(B0.y, B1.y);
+                o[c * 12 + 5] = make_float2(-B0.y, -B1.y);
+                for (int e = 6; e < 12; ++e) o[c * 12 + e] = make_float2(0.f, 0.f);
+            }
         }
     }
 }
 
-__device__ __forceinline__ void load4(float2 (&g)[4], const float2* src, float s) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) g[i] = make_float2(src[i].x * s, src[i].y * s);
-}
-
-// Registers <-> shared tile for register run R. Run 0 holds the two entries
-// of each 16-byte chunk in one thread and moves them as one 16-byte access.
+// Registers <-> shared tile for register run R (entry j = k + 16 v at tile
+// coordinate base | j << R). Run 0 moves the two entries of a 16-byte chunk
+// in one 16-byte access.
 template <int R>
-__device__ __forceinline__ void smem_read(float2 (&v)[32], const float2* tile, uint32_t tid) {
+__device__ __forceinline__ void smem_read(float2 (&P)[16], float2 (&Q)[16], const float2* tile, uint32_t tid) {
     uint32_t b = run_base(R, tid);
     asm volatile("" : "+r"(b));
-    if constexpr (R == 0) {
 #pragma unroll
-        for (int j = 0; j < 32; j += 2) {
-            const float4 q = *reinterpret_cast<const float4*>(tile + swz(b | (uint32_t)j));
-            v[j] = make_float2(q.x, q.y);
-            v[j + 1] = make_float2(q.z, q.w);
+    for (int v = 0; v < 2; ++v) {
+        if constexpr (R == 0) {
+#pragma unroll
+            for (int k = 0; k < 16; k += 2) {
+                const float4 e = *reinterpret_cast<const float4*>(tile + swz(b | (uint32_t)(k + 16 * v)));
+                if (v == 0) { P[k].x = e.x; Q[k].x = e.y; P[k + 1].x = e.z; Q[k + 1].x = e.w; }
+                else        { P[k].y = e.x; Q[k].y = e.y; P[k + 1].y = e.z; Q[k + 1].y = e.w; }
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const float2 e = tile[swz(b | ((uint32_t)(k + 16 * v) << R))];
+                if (v == 0) { P[k].x = e.x; Q[k].x = e.y; }
+                else        { P[k].y = e.x; Q[k].y = e.y; }
+            }
         }
-    } else {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] = tile[swz(b | ((uint32_t)j << R))];
     }
 }
 
 template <int R>
-__device__ __forceinline__ void smem_write(const float2 (&v)[32], float2* tile, uint32_t tid) {
+__device__ __forceinline__ void smem_write(const float2 (&P)[16], const float2 (&Q)[16], float2* tile, uint32_t tid) {
     uint32_t b = run_base(R, tid);
     asm volatile("" : "+r"(b));
-    if constexpr (R == 0) {
 #pragma unroll
-        for (int j = 0; j < 32; j += 2)
-            *reinterpret_cast<float4*>(tile + swz(b | (uint32_t)j)) = make_float4(v[j].x, v[j].y, v[j + 1].x, v[j + 1].y);
-    } else {
+    for (int v = 0; v < 2; ++v) {
+        if constexpr (R == 0) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) tile[swz(b | ((uint32_t)j << R))] = v[j];
+            for (int k = 0; k < 16; k += 2) {
+                const float4 e = v == 0 ? make_float4(P[k].x, Q[k].x, P[k + 1].x, Q[k + 1].x)
+                                        : make_float4(P[k].y, Q[k].y, P[k + 1].y, Q[k + 1].y);
+                *reinterpret_cast<float4*>(tile + swz(b | (uint32_t)(k + 16 * v))) = e;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+                tile[swz(b | ((uint32_t)(k + 16 * v) << R))] =
+                    v == 0 ? make_float2(P[k].x, Q[k].x) : make_float2(P[k].y, Q[k].y);
+        }
     }
 }
 
 // Hand the tile from register run R1 to run R2: every thread writes its
 // entries back to their own slots, then reads the slots of its new run.
 template <int R1, int R2>
-__device__ __forceinline__ void transpose(float2 (&v)[32], float2* tile, uint32_t tid) {
-    smem_write<R1>(v, tile, tid);
+__device__ __forceinline__ void transpose(float2 (&P)[16], float2 (&Q)[16], float2* tile, uint32_t tid) {
+    smem_write<R1>(P, Q, tile, tid);
     __syncthreads();
-    smem_read<R2>(v, tile, tid);
+    smem_read<R2>(P, Q, tile, tid);
 }
 
 template <class SH, int I, int R>
-__device__ __forceinline__ void apply_step(float2 (&v)[32], const float2* sg, uint32_t xmask,
-                                           float scale, uint32_t tid) {
+__device__ __forceinline__ void apply_step(float2 (&P)[16], float2 (&Q)[16], const float2* sc,
+                                           uint32_t xmask, float scale, uint32_t tid) {
     constexpr StepSpec sp = step_spec(SH::TYPE, SH::M, I);
-    constexpr int s = SH::C + sp.t;
-    constexpr int K = s - R;
+    constexpr int K = SH::C + sp.t - R;
     static_assert(K >= 0 && K < REG_BITS, "step target outside its register run");
-    const float sc = (I == 0) ? scale : 1.0f;
+    constexpr int kind = step_kind<SH>(I);
+    // control: -1 none, 0..4 run bit, 5 external (a thread bit)
+    constexpr int u = SH::C + sp.c;
+    constexpr int CK = sp.c < 0 ? -1 : (in_run(u, R) ? u - R : 5);
+    const float s = (I == 0) ? scale : 1.0f;
     asm volatile("" ::: "memory");  // load each step's coefficients just before it
-    const float2* g = sg + I * 16 + (((xmask >> I) & 1u) ? 8 : 0);
-    if constexpr (sp.c < 0) {
-        float2 gg[4];
-        load4(gg, g, sc);
-        step_plain<K>(v, gg);
+    const float2* cf = sc + (I * 2 + (int)((xmask >> I) & 1u)) * CO;
+    float2 c0[12], c1[12];
+    if constexpr (CK == 5) {
+        const uint32_t c = (run_base(R, tid) >> u) & 1u;
+        load_cf(c0, cf + 12 * c, s);
     } else {
-        constexpr int u = SH::C + sp.c;
-        if constexpr (in_run(u, R)) {
-            float2 g0[4], g1[4];
-            load4(g0, g, sc);
-            load4(g1, g + 4, sc);
-            step_ctrl<K, u - R>(v, g0, g1);
-        } else {
-            const uint32_t c = (run_base(R, tid) >> u) & 1u;
-            float2 gg[4];
-            load4(gg, g + 4 * c, sc);
-            step_plain<K>(v, gg);
-        }
+        load_cf(c0, cf, s);
+    }
+    if constexpr (CK >= 0 && CK < 4) load_cf(c1, cf + 12, s);
+    if constexpr (kind == KIND_VT) {
+        step_lanes<CK>(P, Q, c0, c1);
+    } else {
+        step_pairs<K, (kind == KIND_VC ? 4 : CK)>(P, Q, c0, c1);
     }
 }
 
 template <class SH, int I>
-__device__ __forceinline__ void run_steps(float2 (&v)[32], const float2* sg, uint32_t xmask,
+__device__ __forceinline__ void run_steps(float2 (&P)[16], float2 (&Q)[16], const float2* sc, uint32_t xmask,
                                           float scale, uint32_t tid, float2* tile) {
     if constexpr (I < SH::NS) {
         constexpr int R = SH::run_of(I);
         constexpr int RP = (I == 0) ? SH::first_run() : SH::run_of(I - 1);
-        if constexpr (R != RP) transpose<RP, R>(v, tile, tid);
-        apply_step<SH, I, R>(v, sg, xmask, scale, tid);
-        run_steps<SH, I + 1>(v, sg, xmask, scale, tid, tile);
+        if constexpr (R != RP) transpose<RP, R>(P, Q, tile, tid);
+        apply_step<SH, I, R>(P, Q, sc, xmask, scale, tid);
+        run_steps<SH, I + 1>(P, Q, sc, xmask, scale, tid, tile);
     }
 }
 
-// Global offset (entries, from the tile origin) of tile coordinate idx.
 template <class SH>
 __device__ __forceinline__ int64_t tile_addr(uint32_t idx, int lo) {
     if constexpr (SH::BOT) return idx;
@@ -274,16 +386,18 @@ __device__ __forceinline__ void issue_tile(const PassParams& p, int64_t gt, floa
     }
 }
 
+
 template <int TYPE, int M>
-__global__ void __launch_bounds__(PASS_THREADS, 1) pass_kernel(const PassParams p) {
+__global__ void __launch_bounds__(PASS_THREADS, PASS_CTAS_PER_SM) pass_kernel(const PassParams p) {
     using SH = Shape<TYPE, M>;
     static_assert(SH::valid(), "invalid pass shape");
+    static_assert(SH::NS <= 32, "step mask holds 32 steps");
     constexpr int NS = SH::NS;
     extern __shared__ __align__(16) float2 smem[];
-    float2* sg = smem + PASS_STAGES * TILE;
+    float2* sc = smem + PASS_STAGES * TILE;
     const uint32_t tid = threadIdx.x;
 
-    for (int i = tid; i < NS * 16; i += PASS_THREADS) sg[i] = reinterpret_cast<const float2*>(p.steps)[i];
+    stage_coefficients<SH>(p.steps, sc, tid);
 
     // prologue: the first PASS_STAGES-1 tiles of this CTA
 #pragma unroll
@@ -296,6 +410,9 @@ __global__ void __launch_bounds__(PASS_THREADS, 1) pass_kernel(const PassParams 
     const int64_t tmask = ((int64_t)1 << p.tile_shift) - 1;
     float runmax = 0.0f;
     int64_t cur_b = -1;
+    int cur_s = 0;
+    float scale = 1.0f;
+    uint32_t xmask = 0;
     int stage = 0;
     for (int64_t gt = blockIdx.x; gt < p.ntiles; gt += gridDim.x) {
         {   // keep PASS_STAGES-1 tiles in flight
@@ -306,31 +423,32 @@ __global__ void __launch_bounds__(PASS_THREADS, 1) pass_kernel(const PassParams 
         }
         const int64_t b = gt >> p.tile_shift;
         const int64_t t = gt & tmask;
-        if (b != cur_b) {
+        if (b != cur_b) {  // per-bitstring state, read once per batch element
             if (cur_b >= 0) flush_max(runmax, p.maxs + cur_b * p.sstride + p.slot + 1);
             runmax = 0.0f;
             cur_b = b;
+            cur_s = rescale_exp(__uint_as_float(p.maxs[b * p.sstride + p.slot]));
+            scale = ldexpf(1.0f, cur_s);
+            const uint8_t* xb = p.bits + b * p.n;
+            xmask = 0;
+            if (p.xs_step0 >= 0) xmask |= (xb[p.xs_q0] ? 1u : 0u) << p.xs_step0;
+            if (p.xs_step1 >= 0) xmask |= (xb[p.xs_q1] ? 1u : 0u) << p.xs_step1;
         }
-        const int s = rescale_exp(__uint_as_float(p.maxs[b * p.sstride + p.slot]));
-        if (t == 0 && tid == 0) p.exps[b * p.sstride + p.slot + 1] = s;
-        const float scale = ldexpf(1.0f, s);
-        const uint8_t* xb = p.bits + b * p.n;
-        uint32_t xmask = 0;
-        if (p.xs_step0 >= 0) xmask |= (xb[p.xs_q0] ? 1u : 0u) << p.xs_step0;
-        if (p.xs_step1 >= 0) xmask |= (xb[p.xs_q1] ? 1u : 0u) << p.xs_step1;
+        if (t == 0 && tid == 0) p.exps[b * p.sstride + p.slot + 1] = cur_s;
 
         float2* tile = smem + stage * TILE;
         cp_async_wait<PASS_STAGES - 1>();
         __syncthreads();
 
-        float2 v[32];
-        smem_read<SH::first_run()>(v, tile, tid);
-        run_steps<SH, 0>(v, sg, xmask, scale, tid, tile);
+        float2 P[16], Q[16];
+        smem_read<SH::first_run()>(P, Q, tile, tid);
+        run_steps<SH, 0>(P, Q, sc, xmask, scale, tid, tile);
         constexpr int RL = SH::run_of(NS - 1);
         constexpr int RS = SH::last_run();
-        if constexpr (RL != RS) transpose<RL, RS>(v, tile, tid);
+        if constexpr (RL != RS) transpose<RL, RS>(P, Q, tile, tid);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) runmax = fmaxf(runmax, fmaxf(fabsf(v[j].x), fabsf(v[j].y)));
+        for (int k = 0; k < 16; ++k)
+            runmax = fmaxf(runmax, fmaxf(fmaxf(fabsf(P[k].x), fabsf(P[k].y)), fmaxf(fabsf(Q[k].x), fabsf(Q[k].y))));
         {
             float2* dst = p.B + b * p.b_stride + tile_origin<SH>(t, p.lo);
             const uint32_t c0 = run_base(RS, tid);
@@ -338,11 +456,17 @@ __global__ void __launch_bounds__(PASS_THREADS, 1) pass_kernel(const PassParams 
             int64_t st = tile_addr<SH>(1u << RS, p.lo);
             asm volatile("" : "+l"(off0), "+l"(st));
 #pragma unroll
-            for (int g = 0; g < 4; ++g) {
-                float2* q = dst + off0 + (int64_t)(8 * g) * st;
-                asm volatile("" : "+l"(q));
+            for (int v = 0; v < 2; ++v) {
 #pragma unroll
-                for (int j = 0; j < 8; ++j) q[j * st] = v[8 * g + j];
+                for (int g = 0; g < 2; ++g) {
+                    float2* q = dst + off0 + (int64_t)(16 * v + 8 * g) * st;
+                    asm volatile("" : "+l"(q));
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int k = 8 * g + j;
+                        q[j * st] = v == 0 ? make_float2(P[k].x, Q[k].x) : make_float2(P[k].y, Q[k].y);
+                    }
+                }
             }
         }
         __syncthreads();  // every thread is done with this stage before it is refilled
@@ -354,7 +478,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 1) pass_kernel(const PassParams 
 
 template <int TYPE, int M>
 constexpr int pass_smem_bytes() {
-    return (PASS_STAGES * TILE + pass_nsteps(TYPE, M) * 16) * (int)sizeof(float2);
+    return (PASS_STAGES * TILE + pass_nsteps(TYPE, M) * 2 * CO) * (int)sizeof(float2);
 }
 
 // Launchers, one translation unit per pass type (pass_t<type>.cu).
@@ -368,12 +492,16 @@ cudaError_t launch_pass_t6(int M, const PassParams& p, int grid, cudaStream_t st
 
 template <int TYPE, int M>
 cudaError_t launch_one(const PassParams& p, int grid, cudaStream_t st) {
+    if constexpr (!Shape<TYPE, M>::valid()) {
+        return cudaErrorInvalidValue;
+    } else {
     constexpr int smem = pass_smem_bytes<TYPE, M>();
     cudaError_t e = cudaFuncSetAttribute(pass_kernel<TYPE, M>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     pass_kernel<TYPE, M><<<grid, PASS_THREADS, smem, st>>>(p);
     return cudaGetLastError();
+    }
 }
 
 #define TB_DEFINE_LAUNCH_PASS(TYPE, NAME)                                         \

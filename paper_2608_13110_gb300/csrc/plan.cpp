@@ -85,15 +85,16 @@ static std::vector<int> partition(int h, int mmax, int b, int t) {
     if (need > 0) {
         // as few middle windows as the limit allows, sizes as even as
         // possible, the larger ones first (they sit right above bit 0's window)
-        const int cnt = (need + (mmax - 1) - 1) / (mmax - 1);
+        const int mm = std::min(mmax, MAX_WINDOW_HIGH);
+        const int cnt = (need + (mm - 1) - 1) / (mm - 1);
         for (int j = 0; j < cnt; ++j) {
             const int add = need / cnt + (j < need % cnt ? 1 : 0);
             sizes.push_back(add + 1);
         }
     }
     sizes.push_back(t);
-    for (int m : sizes)
-        if (m < MIN_WINDOW || m > MAX_WINDOW) return {};
+    for (size_t j = 0; j < sizes.size(); ++j)
+        if (sizes[j] < MIN_WINDOW || sizes[j] > (j == 0 ? MAX_WINDOW : MAX_WINDOW_HIGH)) return {};
     return sizes;
 }
 
@@ -114,8 +115,8 @@ static bool build_passes(Plan& P, const std::vector<int>& sizes, std::vector<Pas
         hi[j] = lo[j] + sizes[j] - 1;
     }
     if (hi[K] != h - 1) return false;
-    // a window above address bit 0 shares its tile with the 13-M lowest
-    // address bits, so it must lie entirely above them
+    // a window above address bit 0 shares its tile with the TILE_BITS-M
+    // lowest address bits, so it must lie entirely above them
     for (int j = 1; j <= K; ++j)
         if (lo[j] + sizes[j] < TILE_BITS) return false;
     // window of each step
