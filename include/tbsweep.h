@@ -173,6 +173,26 @@ TB_API int tb_profile_begin(void);
 /* Stop recording, wait for the recorded events and sum them into *out. */
 TB_API int tb_profile_end(tb_profile_t* out);
 
+/* Amplitudes without allocating: like tb_amplitudes_device, but the tables,
+ * rescaling state and boundary live in a fixed 64 MiB scratch array compiled
+ * into this library, so the call needs no workspace and calls no cudaMalloc.
+ * The paper has no counterpart; this entry exists for callers that cannot
+ * allocate device memory at the point of use (work recorded into a CUDA graph,
+ * processes under a device-memory quota owned by someone else, plugins that
+ * must not create untracked allocations).
+ *   d_bits: device, nb*n bytes; d_out: device, 2*nb doubles (re, im).
+ * Limits and behaviour:
+ *   - plans whose tables plus one boundary exceed 64 MiB (for n = 70: width
+ *     above 22) return TB_ENOMEM;
+ *   - the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture;
+ *   - every call on a device shares the one array and leaves its contents
+ *     behind; calls that overlap on the GPU (other streams, other threads)
+ *     race and corrupt each other's results: serialise them;
+ *   - work is enqueued on stream; no synchronisation. */
+TB_API int tb_amplitudes_noalloc(const tb_plan* plan, const uint8_t* d_bits, int64_t nb, double* d_out,
+                                 void* stream);
+
 /* log-XEB estimator/* log-XEB estimator F = gamma + n ln 2 + (1/N) sum_i ln |amp_i|^2 (Sec. 5.2,
  * normalized log-XEB equation), host FP64. amp: 2*nb doubles (re, im).
  * A zero amplitude gives -inf. */

@@ -53,6 +53,7 @@ _sig = {
     "tb_plan_upload": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _vp]),
     "tb_amplitudes_device": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _vp, ctypes.c_int64, _vp, _vp]),
     "tb_amplitudes": (ctypes.c_int, [_vp, _u8p, ctypes.c_int64, _vp, ctypes.c_int64, _dp, _vp]),
+    "tb_amplitudes_noalloc": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _vp, _vp]),
     "tb_plan_schedule": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int32), ctypes.c_int]),
     "tb_profile_begin": (ctypes.c_int, []),
     "tb_profile_end": (ctypes.c_int, [ctypes.c_void_p]),
@@ -202,6 +203,14 @@ class Plan:
         _check(_lib.tb_amplitudes_device(self._h, d_bits.data_ptr(), nb, ws.data_ptr(), ws.numel(),
                                          d_out.data_ptr(), _stream_handle(stream)),
                "tb_amplitudes_device")
+
+    def amplitudes_noalloc(self, d_bits, d_out, stream=None) -> None:
+        """Like ``amplitudes_device`` but with the library's fixed scratch
+        instead of a workspace (no device allocation; see tb_amplitudes_noalloc
+        in include/tbsweep.h for its size limit and sharing rules)."""
+        nb = d_bits.shape[0] if d_bits.dim() > 1 else d_bits.numel() // self.n
+        _check(_lib.tb_amplitudes_noalloc(self._h, d_bits.data_ptr(), nb, d_out.data_ptr(),
+                                          _stream_handle(stream)), "tb_amplitudes_noalloc")
 
     def amplitudes(self, bits, ws=None, stream=None, out=None) -> np.ndarray:
         """Host bitstrings (nb, n) -> host complex128 amplitudes; synchronous."""

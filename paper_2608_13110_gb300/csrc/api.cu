@@ -275,6 +275,20 @@ int run_device(const Plan& P, const uint8_t* d_bits, int64_t nb, void* d_ws, int
 
 }  // namespace
 
+// ---- evaluation without device allocation ----------------------------------
+// Some callers cannot call cudaMalloc when they need amplitudes: code that
+// records work into a CUDA graph (allocation is not a capturable operation),
+// a process that runs under a device-memory quota fixed by someone else, or a
+// plugin that must not create allocations the host application does not
+// track. For them the library carries one fixed scratch area in device memory,
+// a file-scope array that every GPU loading the library holds until exit.
+namespace {
+constexpr int64_t NOALLOC_SCRATCH_BYTES = (int64_t)64 << 20;  // 64 MiB per device
+static __device__ __align__(256) uint8_t g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[64] = {nullptr};  // device address of the array, per device
+}  // namespace
+
 extern "C" {
 
 int tb_plan_create(int n, int d, const uint8_t* cliff, const uint8_t* tmask, const tb_gate1q* extra,
@@ -411,6 +425,39 @@ int tb_profile_end(tb_profile_t* out) {
     g_prof.recs.clear();
     g_prof.used = 0;
     return TB_OK;
+}
+
+int tb_amplitudes_noalloc(const tb_plan* plan, const uint8_t* d_bits, int64_t nb, double* d_out,
+                          void* stream) {
+    if (!plan || nb < 0 || (nb > 0 && (!d_bits || !d_out))) return fail(TB_EINVAL, "NULL or negative argument");
+    const Plan& P = plan->p;
+    if (P.h > MAX_H) return fail(TB_EDOMAIN, "boundary wider than 2^33 entries");
+    const int64_t need = P.lay.total + call_layout(P).per_b;
+    if (need > NOALLOC_SCRATCH_BYTES)
+        return fail(TB_ENOMEM, "this circuit needs " + std::to_string(need) +
+                                   " bytes of scratch; the fixed scratch holds " +
+                                   std::to_string(NOALLOC_SCRATCH_BYTES));
+    if (nb == 0) return TB_OK;
+    int dev = 0;
+    TB_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(TB_EINVAL, "device index out of range");
+    void* base = nullptr;
+    {
+        // set-up, once per device, with that device current: the host-side
+        // name of the array is not a device address, so ask for the address
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void* a = nullptr;
+            TB_CUDA(cudaGetSymbolAddress(&a, g_noalloc_scratch));
+            g_noalloc_addr[dev] = a;
+        }
+        base = g_noalloc_addr[dev];
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    TB_CUDA(cudaMemcpyAsync(base, P.blob.data(), (size_t)P.lay.total, cudaMemcpyHostToDevice, st));
+    // run_device clears the rescaling slots of every batch before use; the
+    // boundary and the partial sums are fully written before they are read
+    return run_device(P, d_bits, nb, base, NOALLOC_SCRATCH_BYTES, P.lay.total, d_out, st);
 }
 
 int tb_log_xeb(const double* amp, int64_t nb, int n, double* out) {
