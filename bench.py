@@ -202,7 +202,11 @@ def run_ours(args, rank, world, local):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     nb = args.nb
-    c = W.precision_70_64(replica=rank, nb=nb)
+    if args.shape:  # profiling aid: a smaller circuit with the same statistics
+        n_, d_ = (int(v) for v in args.shape.split(","))
+        c = W.random_circuit(n_, d_, None, nb, 4000 + 100 * rank + d_)
+    else:
+        c = W.precision_70_64(replica=rank, nb=nb)
     plan = tb.Plan.from_circuit(c)
     info = plan.info
     h = info["boundary_bits"]
@@ -292,13 +296,14 @@ def run_ours(args, rank, world, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--nb", type=int, default=16)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--shape", default="", help="n,d of a smaller circuit (profiling only; not the reported workload)")
     args = ap.parse_args()
     if args.impl == "reference":
         rank, world, _ = dist_setup("gloo")
