@@ -293,6 +293,145 @@ def run_ours(args, rank, world, local):
         print(json.dumps(line))
 
 
+def run_batch_workload(args, rank, world, local):
+    """64 circuits of uneven size (n ~ U[20,70], d ~ U{16..48}, T density
+    0.095, 32 bitstrings each = 2048 amplitudes) recorded into one CUDA graph
+    with autotuned window sizes, against the plain path (one call per circuit,
+    back to back on one stream)."""
+    import torch
+    import paper_2608_13110_gb300 as tb
+    from paper_2608_13110_gb300 import autotune
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    nb = 32
+    circuits = W.batch_uneven(64, nb, seed0=3000 + 1000 * rank)
+    t0 = time.perf_counter()
+    plans = [autotune.tuned_plan(c, nb=nb) for c in circuits]
+    tune_s = time.perf_counter() - t0
+    d_bits = [torch.from_numpy(c.bits).to(dev) for c in circuits]
+    out_b = [torch.empty((nb, 2), dtype=torch.float64, device=dev) for _ in circuits]
+    out_p = [torch.empty((nb, 2), dtype=torch.float64, device=dev) for _ in circuits]
+    t0 = time.perf_counter()
+    batch = tb.Batch(list(zip(plans, d_bits, out_b)))
+    record_s = time.perf_counter() - t0
+    wss = []
+    for pl in plans:
+        ws = pl.alloc_workspace(nb)
+        pl.upload(ws)
+        wss.append(ws)
+    stream = torch.cuda.current_stream(dev)
+
+    def plain():
+        for pl, db, ws, o in zip(plans, d_bits, wss, out_p):
+            pl.amplitudes_device(db, ws, o, stream)
+
+    def timed(fn, k):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / 1e3
+
+    for _ in range(args.warmup):
+        batch.launch(stream)
+        plain()
+    torch.cuda.synchronize(dev)
+    barrier(world, dev)
+    clocks = ClockSampler(local)
+    t_b = timed(lambda: batch.launch(stream), args.steps)
+    t_p = timed(plain, args.steps)
+    clk = clocks.stop()
+    same = all(torch.equal(a, b) for a, b in zip(out_b, out_p))
+    t_b = max_over_ranks(t_b, world, dev)
+    t_p = max_over_ranks(t_p, world, dev)
+    namps = 64 * nb
+    line = {"metric": "amplitudes/s (64 uneven brickwork circuits, 2048 amplitudes, one graph launch)",
+            "value": world * namps * args.steps / t_b, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_b / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "complex64", "data": "synthetic",
+            "config": {"workload": "64 circuits n~U[20,70], d~U{16..48} even, T density 0.095, 32 bitstrings each",
+                       "widths": sorted({c.d // 2 for c in circuits}), "autotune_s": tune_s,
+                       "graph_record_s": record_s, "parallelism": f"replicas x{world}"},
+            "plain": {"value": world * namps * args.steps / t_p, "unit": UNIT, "ms_per_step": 1e3 * t_p / args.steps,
+                      "how": "one tb_amplitudes_device call per circuit, back to back on one stream"},
+            "identical_to_plain": bool(same), "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def run_serve_workload(args, rank, world, local):
+    """Poisson stream (mean 20 requests/s) of amplitude requests, n ~ U[16,70],
+    d even ~ U{8..44} (width <= 22), 1..256 bitstrings each,
+    through the serving runtime (160 GB budget, continuous admission) against
+    the plain path: the same requests one at a time in arrival order."""
+    import threading
+    import torch
+    import paper_2608_13110_gb300 as tb
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    reqs = W.serving_stream(args.requests, rate_hz=20.0, seed=5000 + 1000 * rank, max_width=22)
+    plans = [tb.Plan.from_circuit(c) for _, c in reqs]
+    namps = sum(c.bits.shape[0] for _, c in reqs)
+    # warm the kernels and the allocator
+    for pl, (_, c) in list(zip(plans, reqs))[: args.warmup]:
+        pl.amplitudes(c.bits[:1])
+    torch.cuda.synchronize(dev)
+
+    srv = tb.Server(hbm_budget_bytes=160 * 10**9, slots=8, device=local, pinned_bytes=256 << 20)
+    tickets = [None] * len(reqs)
+    t0 = time.perf_counter()
+
+    def submitter():
+        for i, ((t_arr, c), pl) in enumerate(zip(reqs, plans)):
+            dt = t0 + t_arr - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            tickets[i] = srv.submit(pl, c.bits)
+
+    clocks = ClockSampler(local)
+    th = threading.Thread(target=submitter)
+    th.start()
+    th.join()
+    res_srv = [srv.wait(t)[0] for t in tickets]
+    t_srv = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+
+    # plain path: one request at a time, in arrival order, same arrival times
+    lat = []
+    res_plain = []
+    t0 = time.perf_counter()
+    for (t_arr, c), pl in zip(reqs, plans):
+        dt = t0 + t_arr - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        res_plain.append(pl.amplitudes(c.bits))
+        lat.append(time.perf_counter() - (t0 + t_arr))
+    t_plain = time.perf_counter() - t0
+    clk = clocks.stop()
+    err = max(float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)) for a, b in zip(res_srv, res_plain))
+    lat.sort()
+    q = lambda f: lat[min(len(lat) - 1, int(f * (len(lat) - 1) + 0.5))]
+    line = {"metric": "amplitudes/s and p50/p99 latency, Poisson request stream (served)",
+            "value": world * namps / max_over_ranks(t_srv, world, dev), "unit": UNIT, "n_gpus": world,
+            "steps": 1, "warmup": args.warmup, "ms_per_step": 1e3 * t_srv, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "complex64", "data": "synthetic",
+            "config": {"workload": f"{len(reqs)} requests, Poisson 20/s, n~U[16,70], d even <= 44 (width <= 22), "
+                                   "1..256 bitstrings", "amplitudes": namps, "hbm_budget_bytes": 160 * 10**9,
+                       "slots": 8, "parallelism": f"replicas x{world}"},
+            "latency_s": {"p50": st["p50_latency_s"], "p99": st["p99_latency_s"], "mean": st["mean_latency_s"]},
+            "server": {"peak_concurrent": st["peak_concurrent"], "peak_bytes_in_use": st["peak_bytes_in_use"]},
+            "plain": {"value": world * namps / max_over_ranks(t_plain, world, dev), "unit": UNIT,
+                      "latency_s": {"p50": q(0.5), "p99": q(0.99), "mean": sum(lat) / len(lat)},
+                      "how": "each request alone through tb_amplitudes, in arrival order"},
+            "max_rel_l2_served_vs_plain": err, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -303,6 +442,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="n70d64", choices=("n70d64", "batch", "serve"),
+                    help="n70d64: the headline metric; batch: 64 uneven circuits in one graph; "
+                         "serve: Poisson request stream through the serving runtime")
+    ap.add_argument("--requests", type=int, default=200, help="requests in the serve workload")
     ap.add_argument("--shape", default="", help="n,d of a smaller circuit (profiling only; not the reported workload)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -310,7 +453,12 @@ def main():
         run_reference(args, rank, world)
     else:
         rank, world, local = dist_setup("nccl")
-        run_ours(args, rank, world, local)
+        if args.workload == "batch":
+            run_batch_workload(args, rank, world, local)
+        elif args.workload == "serve":
+            run_serve_workload(args, rank, world, local)
+        else:
+            run_ours(args, rank, world, local)
     if _env_int("WORLD_SIZE", 1) > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

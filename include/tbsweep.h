@@ -155,6 +155,91 @@ TB_API int tb_amplitudes(const tb_plan* plan, const uint8_t* bits, int64_t nb, v
  * or -1 for a NULL plan. */
 TB_API int tb_plan_schedule(const tb_plan* plan, int32_t* sched, int cap);
 
+/* ---- Batches of circuits -------------------------------------------------
+ * Many independent circuits (the paper evaluates many contractions of one
+ * topology as independent jobs, Sec. 5.2; here n and d may differ) recorded
+ * once into a CUDA graph and replayed with one launch. Narrow circuits
+ * (width <= 12) share a single kernel launch, one CTA per bitstring; wider
+ * ones evaluate all their bitstrings side by side and run on parallel graph
+ * branches balanced by estimated cost. */
+typedef struct {
+    const tb_plan* plan;   /* must outlive the batch */
+    const uint8_t* d_bits; /* device, nb*n bytes (x_q at [i*n + q]) */
+    int64_t nb;
+    double* d_out;         /* device, 2*nb doubles (re, im) */
+} tb_batch_item;
+
+typedef struct tb_batch tb_batch;
+
+/* Workspace bytes a batch of these items needs (-1 on a bad item). */
+TB_API int64_t tb_batch_workspace_bytes(const tb_batch_item* items, int nitems);
+
+/* Upload every plan's tables into d_ws (synchronously on stream), then
+ * record the batch's work into a graph. nbranches: parallel branches for the
+ * wide circuits (0 = 4, at most 16). Device pointers of the items are baked
+ * into the graph: rewrite the buffers, not the pointers, between launches. */
+TB_API int tb_batch_create(const tb_batch_item* items, int nitems, void* d_ws, int64_t ws_bytes,
+                           int nbranches, void* stream, tb_batch** out);
+
+/* Replay the recorded batch on stream (asynchronous). */
+TB_API int tb_batch_launch(tb_batch* batch, void* stream);
+
+/* Release a batch (NULL is ignored). */
+TB_API void tb_batch_destroy(tb_batch* batch);
+
+/* ---- Serving -------------------------------------------------------------
+ * A server keeps plans' tables resident on the device and admits amplitude
+ * requests of any size while others run: it owns one device arena (its HBM
+ * budget, allocated once at creation) and `slots` CUDA streams; a dispatcher
+ * thread starts queued requests in arrival order whenever a slot is free and
+ * the arena holds the request's tables plus at least one boundary (tables no
+ * running request uses are evicted least recently used first), polls their
+ * completion events and copies the amplitudes to the caller's buffer. The
+ * paper reuses plan and workspace caches across its contractions (Sec. 5.2);
+ * this applies the same reuse to a stream of independent requests. */
+typedef struct tb_server tb_server;
+
+typedef struct {
+    int64_t hbm_budget_bytes; /* device arena (0 = 16 GiB) */
+    int32_t slots;            /* concurrent requests (0 = 4, at most 64) */
+    int32_t device;           /* CUDA device ordinal */
+    int64_t pinned_bytes;     /* pinned host staging (0 = 64 MiB) */
+} tb_server_opts;
+
+typedef struct {
+    double latency_s; /* submit -> amplitudes in the caller's buffer */
+    double queue_s;   /* submit -> admitted to a slot */
+    double run_s;     /* admitted -> done */
+    int32_t status;
+    int32_t slot;
+} tb_request_stats;
+
+typedef struct {
+    int64_t completed, amplitudes, peak_concurrent, peak_bytes_in_use, queued;
+    double p50_latency_s, p99_latency_s, mean_latency_s;
+} tb_server_stats_t;
+
+/* Create a server (allocates its arena and pinned staging, starts the
+ * dispatcher thread). */
+TB_API int tb_server_create(const tb_server_opts* opts, tb_server** out);
+
+/* Queue nb host bitstrings (nb*n bytes in {0,1}, copied during the call) of
+ * plan; the amplitudes go to out (host, 2*nb doubles) when the request
+ * completes. The plan and out must stay valid until tb_server_wait returns.
+ * A request that cannot fit the budget even alone returns TB_ENOMEM. */
+TB_API int tb_server_submit(tb_server* server, const tb_plan* plan, const uint8_t* bits, int64_t nb,
+                            double* out, int64_t* ticket);
+
+/* Wait for a request (timeout_s < 0: no limit; TB_ETIMEOUT when it runs out,
+ * and the ticket stays valid). Returns the request's status; fills stats. */
+TB_API int tb_server_wait(tb_server* server, int64_t ticket, double timeout_s, tb_request_stats* stats);
+
+/* Counters and latency percentiles of completed requests. */
+TB_API int tb_server_stats(tb_server* server, tb_server_stats_t* out);
+
+/* Finish every queued request, stop the dispatcher, free the server. */
+TB_API void tb_server_destroy(tb_server* server);
+
 /* Kernel timing (tracing aid). While enabled, every kernel this library
  * launches is bracketed by CUDA events on its stream. Classes: 0 boundary
  * passes, 1 row-0 writer, 2 last-row reduction, 3 finalisation, 4 narrow

@@ -55,6 +55,16 @@ _sig = {
     "tb_amplitudes": (ctypes.c_int, [_vp, _u8p, ctypes.c_int64, _vp, ctypes.c_int64, _dp, _vp]),
     "tb_amplitudes_noalloc": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _vp, _vp]),
     "tb_plan_schedule": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int32), ctypes.c_int]),
+    "tb_batch_workspace_bytes": (ctypes.c_int64, [ctypes.c_void_p, ctypes.c_int]),
+    "tb_batch_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _vp, ctypes.c_int64, ctypes.c_int, _vp,
+                                       ctypes.POINTER(_vp)]),
+    "tb_batch_launch": (ctypes.c_int, [_vp, _vp]),
+    "tb_batch_destroy": (None, [_vp]),
+    "tb_server_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_vp)]),
+    "tb_server_submit": (ctypes.c_int, [_vp, _vp, _u8p, ctypes.c_int64, _dp, ctypes.POINTER(ctypes.c_int64)]),
+    "tb_server_wait": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p]),
+    "tb_server_stats": (ctypes.c_int, [_vp, ctypes.c_void_p]),
+    "tb_server_destroy": (None, [_vp]),
     "tb_profile_begin": (ctypes.c_int, []),
     "tb_profile_end": (ctypes.c_int, [ctypes.c_void_p]),
     "tb_log_xeb": (ctypes.c_int, [_dp, ctypes.c_int64, ctypes.c_int, _dp]),
@@ -225,6 +235,114 @@ class Plan:
         _check(_lib.tb_amplitudes(self._h, b.ctypes.data_as(_u8p), nb, ws.data_ptr(), ws.numel(),
                                   out.ctypes.data_as(_dp), _stream_handle(stream)), "tb_amplitudes")
         return out.view(np.complex128).reshape(-1)
+
+
+class _BatchItem(ctypes.Structure):
+    _fields_ = [("plan", _vp), ("d_bits", _vp), ("nb", ctypes.c_int64), ("d_out", _vp)]
+
+
+class Batch:
+    """Many circuits recorded into one CUDA graph (tb_batch_* in the C-ABI).
+
+    items: list of (Plan, d_bits, d_out) with d_bits (nb, n) uint8 and d_out
+    (nb, 2) float64 CUDA tensors; the tensors and plans must stay alive and
+    keep their storage while the batch exists. ``launch()`` replays it."""
+
+    def __init__(self, items, nbranches: int = 0, stream=None):
+        import torch
+        self._keep = list(items)
+        arr = (_BatchItem * len(items))()
+        for i, (plan, d_bits, d_out) in enumerate(items):
+            nb = d_bits.shape[0] if d_bits.dim() > 1 else d_bits.numel() // plan.n
+            arr[i].plan = plan.handle.value
+            arr[i].d_bits = d_bits.data_ptr()
+            arr[i].nb = nb
+            arr[i].d_out = d_out.data_ptr()
+        self._arr = arr
+        need = _lib.tb_batch_workspace_bytes(ctypes.byref(arr), len(items))
+        if need < 0:
+            raise ValueError("bad batch item")
+        dev = items[0][1].device
+        self.ws = torch.empty(int(need), dtype=torch.uint8, device=dev)
+        h = _vp()
+        _check(_lib.tb_batch_create(ctypes.byref(arr), len(items), self.ws.data_ptr(), self.ws.numel(),
+                                    int(nbranches), _stream_handle(stream), ctypes.byref(h)), "tb_batch_create")
+        self._h = h
+
+    def launch(self, stream=None) -> None:
+        _check(_lib.tb_batch_launch(self._h, _stream_handle(stream)), "tb_batch_launch")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.tb_batch_destroy(h)
+            self._h = None
+
+
+class _ServerOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("slots", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("pinned_bytes", ctypes.c_int64)]
+
+
+class _ReqStats(ctypes.Structure):
+    _fields_ = [("latency_s", ctypes.c_double), ("queue_s", ctypes.c_double), ("run_s", ctypes.c_double),
+                ("status", ctypes.c_int32), ("slot", ctypes.c_int32)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("amplitudes", ctypes.c_int64), ("peak_concurrent", ctypes.c_int64),
+                ("peak_bytes_in_use", ctypes.c_int64), ("queued", ctypes.c_int64),
+                ("p50_latency_s", ctypes.c_double), ("p99_latency_s", ctypes.c_double),
+                ("mean_latency_s", ctypes.c_double)]
+
+
+class Server:
+    """Amplitude server (tb_server_* in the C-ABI): resident plan tables, an
+    HBM budget allocated once, ``slots`` requests running concurrently and
+    queued requests admitted as slots and memory free up."""
+
+    def __init__(self, hbm_budget_bytes: int = 16 << 30, slots: int = 4, device: int = 0,
+                 pinned_bytes: int = 64 << 20):
+        o = _ServerOpts(int(hbm_budget_bytes), int(slots), int(device), int(pinned_bytes))
+        h = _vp()
+        _check(_lib.tb_server_create(ctypes.byref(o), ctypes.byref(h)), "tb_server_create")
+        self._h = h
+        self._pending = {}
+
+    def submit(self, plan: "Plan", bits) -> int:
+        b = _u8(bits)
+        if b.ndim == 1:
+            b = b.reshape(1, -1)
+        out = np.empty((b.shape[0], 2), np.float64)
+        t = ctypes.c_int64(0)
+        _check(_lib.tb_server_submit(self._h, plan.handle, b.ctypes.data_as(_u8p), b.shape[0],
+                                     out.ctypes.data_as(_dp), ctypes.byref(t)), "tb_server_submit")
+        self._pending[t.value] = (plan, out)
+        return t.value
+
+    def wait(self, ticket: int, timeout: float = -1.0):
+        """(complex128 amplitudes, {latency_s, queue_s, run_s, slot})."""
+        st = _ReqStats()
+        rc = _lib.tb_server_wait(self._h, ticket, float(timeout), ctypes.byref(st))
+        if rc == TB_ETIMEOUT:
+            raise TimeoutError(f"request {ticket} still running")
+        plan, out = self._pending.pop(ticket)
+        _check(rc, "tb_server_wait")
+        return out.view(np.complex128).reshape(-1), {f: getattr(st, f) for f, _ in _ReqStats._fields_}
+
+    def stats(self) -> dict:
+        st = _ServerStats()
+        _check(_lib.tb_server_stats(self._h, ctypes.byref(st)), "tb_server_stats")
+        return {f: getattr(st, f) for f, _ in _ServerStats._fields_}
+
+    def close(self) -> None:
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.tb_server_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
 
 
 class _Profile(ctypes.Structure):

@@ -16,9 +16,11 @@
 #include "misc_kernels.cuh"
 #include "pass_kernel.cuh"
 #include "tb_plan.h"
+#include "tb_run.h"
 #include "tbsweep.h"
 
-namespace {
+namespace tb {
+namespace rt {
 
 thread_local std::string g_err;
 
@@ -26,15 +28,6 @@ int fail(int code, const std::string& msg) {
     g_err = msg;
     return code;
 }
-
-#define TB_CUDA(call)                                                                   \
-    do {                                                                                \
-        cudaError_t e_ = (call);                                                        \
-        if (e_ != cudaSuccess)                                                          \
-            return fail(TB_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
-    } while (0)
-
-using namespace tb;
 
 // ---- optional per-launch timing -------------------------------------------
 enum { PC_PASS = 0, PC_INIT = 1, PC_REDUCE = 2, PC_FINAL = 3, PC_SMALL = 4, PC_N = 5 };
@@ -78,17 +71,6 @@ struct ProfScope {
         cudaEvent_t e = g_prof.take(i1);
         if (e && cudaEventRecord(e, st) == cudaSuccess) g_prof.recs.push_back({cls, bytes, i0, i1});
     }
-};
-
-constexpr int64_t DEFAULT_BATCH_ENTRIES = (int64_t)1 << 30;  // 8 GiB of boundaries
-
-struct CallLayout {
-    int nslots = 0;
-    int64_t scale_bytes = 0;    // per batch element
-    int red_blocks = 0;         // reduction blocks per batch element
-    int64_t partial_bytes = 0;  // per batch element
-    int64_t boundary_bytes = 0; // per batch element
-    int64_t per_b = 0;
 };
 
 bool small_path(const Plan& P) { return P.h <= SMALL_H_MAX; }
@@ -273,7 +255,11 @@ int run_device(const Plan& P, const uint8_t* d_bits, int64_t nb, void* d_ws, int
     return TB_OK;
 }
 
-}  // namespace
+}  // namespace rt
+}  // namespace tb
+
+using namespace tb;
+using namespace tb::rt;
 
 // ---- evaluation without device allocation ----------------------------------
 // Some callers cannot call cudaMalloc when they need amplitudes: code that
@@ -303,6 +289,7 @@ int tb_plan_create(int n, int d, const uint8_t* cliff, const uint8_t* tmask, con
             delete p;
             return fail(rc, err);
         }
+        p->p.uid = next_plan_uid();
         *out = p;
         return TB_OK;
     } catch (const std::bad_alloc&) {

@@ -207,11 +207,9 @@ __device__ int small_rescale(float2* Bs, int N, float* red) {
     return s;
 }
 
-__global__ void __launch_bounds__(SMALL_THREADS) small_kernel(const SmallParams p) {
-    extern __shared__ float2 Bs[];
-    __shared__ float redf[SMALL_THREADS / 32];
-    __shared__ double2 redd[SMALL_THREADS / 32];
-    const int b = blockIdx.x;
+// Bitstring b of one narrow plan, the whole sweep in shared memory (Bs holds
+// 2^h entries).
+__device__ void small_sweep(const SmallParams& p, int b, float2* Bs, float* redf, double2* redd) {
     const uint8_t* xb = p.bits + (int64_t)b * p.n;
     const int h = p.h, N = 1 << h;
     const int x0 = xb[0] ? 1 : 0;
@@ -251,6 +249,36 @@ __global__ void __launch_bounds__(SMALL_THREADS) small_kernel(const SmallParams 
         p.out[2 * b] = scalbn(tot.x, -Si);
         p.out[2 * b + 1] = scalbn(tot.y, -Si);
     }
+}
+
+__global__ void __launch_bounds__(SMALL_THREADS) small_kernel(const SmallParams p) {
+    extern __shared__ float2 Bs[];
+    __shared__ float redf[SMALL_THREADS / 32];
+    __shared__ double2 redd[SMALL_THREADS / 32];
+    small_sweep(p, blockIdx.x, Bs, redf, redd);
+}
+
+// Several narrow plans in one launch: block i evaluates bitstring
+// i - first_block of the item whose block range holds i.
+__global__ void __launch_bounds__(SMALL_THREADS) small_multi_kernel(const SmallItem* items, int nitems) {
+    extern __shared__ float2 Bs[];
+    __shared__ float redf[SMALL_THREADS / 32];
+    __shared__ double2 redd[SMALL_THREADS / 32];
+    int lo = 0, hi = nitems - 1;
+    const int64_t blk = blockIdx.x;
+    while (lo < hi) {  // last item with first_block <= blk
+        const int mid = (lo + hi + 1) >> 1;
+        if (items[mid].first_block <= blk) lo = mid;
+        else hi = mid - 1;
+    }
+    const SmallParams p = items[lo].p;
+    small_sweep(p, (int)(blk - items[lo].first_block), Bs, redf, redd);
+}
+
+cudaError_t launch_small_multi(const SmallItem* d_items, int nitems, int64_t nblocks, int hmax, cudaStream_t st) {
+    const int smem = (1 << hmax) * (int)sizeof(float2);
+    small_multi_kernel<<<(unsigned)nblocks, SMALL_THREADS, smem, st>>>(d_items, nitems);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_small(const SmallParams& p, cudaStream_t st) {

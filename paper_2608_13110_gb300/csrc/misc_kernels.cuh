@@ -65,6 +65,13 @@ struct SmallParams {
     double* out;
 };
 
+// One narrow plan's share of a multi-plan launch: its blocks are
+// [first_block, first_block + p.nb).
+struct SmallItem {
+    SmallParams p;
+    int64_t first_block;
+};
+
 constexpr int REDUCE_THREADS = 256;
 constexpr int MAX_RED_BLOCKS = 1024;
 
@@ -72,5 +79,6 @@ cudaError_t launch_init(const InitParams& p, int grid, cudaStream_t st);
 cudaError_t launch_reduce(const ReduceParams& p, cudaStream_t st);
 cudaError_t launch_finalize(const FinalizeParams& p, cudaStream_t st);
 cudaError_t launch_small(const SmallParams& p, cudaStream_t st);
+cudaError_t launch_small_multi(const SmallItem* d_items, int nitems, int64_t nblocks, int hmax, cudaStream_t st);
 
 }  // namespace tb

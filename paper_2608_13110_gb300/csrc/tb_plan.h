@@ -18,6 +18,7 @@ M2 m2_mul(const M2& A, const M2& B);
 M2 clifford(int k);
 
 struct Plan {
+    uint64_t uid = 0;  // unique per plan object (keys device-resident table caches)
     int n = 0, d = 0, h = 0;
     tb_opts opts{};
     std::vector<M2> U;  // (d+1)*n folded slot gates, index t*n + q
@@ -39,6 +40,8 @@ struct Plan {
     TableLayout lay{};
     std::vector<uint8_t> blob;
 };
+
+uint64_t next_plan_uid();
 
 int plan_build(Plan& P, int n, int d, const uint8_t* cliff, const uint8_t* tmask,
                const tb_gate1q* extra, int n_extra, const tb_opts* opts, std::string& err);

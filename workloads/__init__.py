@@ -157,17 +157,16 @@ def slice_32_48(replica: int = 1, nb: int = 16) -> Circuit:
 
 def serving_stream(n_requests: int, rate_hz: float = 20.0, seed: int = 5000,
                    max_width: int = 33):
-    """Poisson arrivals (mean ``rate_hz``); n ~ U[16,70], d ~ U{8,10,...,66}
-    (kept to width <= max_width), 1..256 uniform bitstrings per request.
-    Returns a list of (arrival_time_s, Circuit)."""
+    """Poisson arrivals (mean ``rate_hz``); n ~ U[16,70], d ~ U{8,10,...,2*max_width}
+    (max_width 33 gives the full d <= 66 range), 1..256 uniform bitstrings per
+    request. Returns a list of (arrival_time_s, Circuit)."""
     rng = np.random.default_rng(seed)
     t = 0.0
     out = []
     for i in range(n_requests):
         t += float(rng.exponential(1.0 / rate_hz))
         n = int(rng.integers(16, 71))
-        d = int(2 * rng.integers(4, 34))
-        d = min(d, 2 * max_width)
+        d = int(2 * rng.integers(4, max_width + 1))
         nb = int(rng.integers(1, 257))
         out.append((t, random_circuit(n, d, None, nb, seed + 100000 + i)))
     return out
