@@ -62,13 +62,33 @@ typedef struct {
     double m[8];
 } tb_gate1q;
 
+/* Pass arithmetic (tb_opts.precision). The split forms compose several
+ * paired steps into a dense block so that tensor cores can apply them; the
+ * paper merges small branch tensors before contracting them with the
+ * boundary (Sec. 5.2) and evaluates the precision of complex64 against
+ * complex128 (Sec. 5.1). */
+enum {
+    TB_PRECISION_FP32 = 0,
+    TB_PRECISION_TF32X3 = 1,
+    TB_PRECISION_BF16X3 = 2
+};
+
 /* Plan options. A zeroed struct (or NULL) selects the defaults. */
 typedef struct {
     int32_t window_bits;  /* largest number of address bits one boundary pass
                              covers (5..10; 0 = default 10) */
     int32_t bottom_bits;  /* size of the window at address bit 0 (5..10; 0 = auto) */
     int32_t top_bits;     /* size of the window ending at bit h-1 (5..10; 0 = auto) */
-    int32_t reserved;
+    int32_t precision;    /* arithmetic of the boundary passes (boundaries wider
+                             than 12 bits; narrower ones always use the first):
+                             TB_PRECISION_FP32 (0, default): the staircase of
+                               controlled 2x2 steps in FP32 FMA;
+                             TB_PRECISION_TF32X3 / TB_PRECISION_BF16X3: the steps
+                               of each pass composed on the host into one dense
+                               complex matrix over 5 (TF32) or 6 (BF16) address
+                               bits and applied with tensor-core MMAs as three
+                               split products hi.hi + hi.lo + lo.hi accumulated
+                               in FP32 (window options are then ignored). */
     int64_t hbm_budget_bytes; /* cap on the boundary batch a call keeps on the
                                  device (0 = no cap beyond the workspace) */
 } tb_opts;
@@ -149,7 +169,8 @@ TB_API int tb_amplitudes(const tb_plan* plan, const uint8_t* bits, int64_t nb, v
 /* The pass schedule: for pass i, sched[3*i] = shape (0 forward window,
  * 1 reversed window, 2 turn at the top, 3 turn at address bit 0, 4 first
  * window of the first absorbed row, 5 last window of a reversed last row,
- * 6 last window of a forward last row), sched[3*i+1] = window bits M,
+ * 6 last window of a forward last row, 7 dense tensor-core block of a
+ * TF32X3 / BF16X3 plan), sched[3*i+1] = window bits M,
  * sched[3*i+2] = address bit of the window's lowest bit. Writes at most cap
  * passes (sched may be NULL when cap == 0) and returns the number of passes,
  * or -1 for a NULL plan. */
@@ -278,7 +299,7 @@ TB_API int tb_profile_end(tb_profile_t* out);
 TB_API int tb_amplitudes_noalloc(const tb_plan* plan, const uint8_t* d_bits, int64_t nb, double* d_out,
                                  void* stream);
 
-/* log-XEB estimator/* log-XEB estimator F = gamma + n ln 2 + (1/N) sum_i ln |amp_i|^2 (Sec. 5.2,
+/* log-XEB estimator F = gamma + n ln 2 + (1/N) sum_i ln |amp_i|^2 (Sec. 5.2,
  * normalized log-XEB equation), host FP64. amp: 2*nb doubles (re, im).
  * A zero amplitude gives -inf. */
 TB_API int tb_log_xeb(const double* amp, int64_t nb, int n, double* out);
@@ -294,6 +315,16 @@ TB_API const char* tb_status_str(int status);
 
 /* Message of the last failed call on this host thread ("" if none). */
 TB_API const char* tb_last_error(void);
+
+/* Device-side wait failures (no counterpart in the paper). Every spin-wait in
+ * the library's kernels (the tensor-core passes wait for their MMAs to
+ * complete) gives up after a bounded number of tries; a kernel that gives up
+ * counts it in a device word, leaves its results undefined and exits cleanly
+ * (its tensor memory released), so the context stays usable.
+ * *count receives the number of failed waits since the last call on the
+ * current device, and the word is cleared. Synchronises the device.
+ * Returns TB_OK, TB_EINVAL (NULL count) or TB_ECUDA. */
+TB_API int tb_device_faults(int32_t* count);
 
 #ifdef __cplusplus
 }

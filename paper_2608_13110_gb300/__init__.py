@@ -30,7 +30,7 @@ class _Gate1q(ctypes.Structure):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("window_bits", ctypes.c_int32), ("bottom_bits", ctypes.c_int32),
-                ("top_bits", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("top_bits", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("hbm_budget_bytes", ctypes.c_int64)]
 
 
@@ -72,6 +72,7 @@ _sig = {
     "tb_plan_destroy": (None, [_vp]),
     "tb_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "tb_last_error": (ctypes.c_char_p, []),
+    "tb_device_faults": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32)]),
 }
 
 class _Lib:
@@ -127,6 +128,26 @@ def _stream_handle(stream):
     return getattr(stream, "cuda_stream", stream)
 
 
+PRECISIONS = {"fp32": 0, "tf32x3": 1, "bf16x3": 2}
+
+
+def _precision_code(p) -> int:
+    """Pass arithmetic: "fp32" (FMA staircase), "tf32x3" or "bf16x3"
+    (tensor-core dense blocks, three split products), or the integer code."""
+    if isinstance(p, str):
+        if p not in PRECISIONS:
+            raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
+        return PRECISIONS[p]
+    return int(p)
+
+
+def device_faults() -> int:
+    """Bounded device waits that gave up since the last call (and clear)."""
+    c = ctypes.c_int32()
+    _check(_lib.tb_device_faults(ctypes.byref(c)), "tb_device_faults")
+    return int(c.value)
+
+
 class Plan:
     """A planned circuit: folded gates, step tables and pass schedule.
 
@@ -135,7 +156,7 @@ class Plan:
 
     def __init__(self, n: int, d: int, cliff=None, tmask=None, extra=None, *,
                  window_bits: int = 0, bottom_bits: int = 0, top_bits: int = 0,
-                 hbm_budget_bytes: int = 0):
+                 hbm_budget_bytes: int = 0, precision=0):
         self.n, self.d = int(n), int(d)
         self._cliff = None if cliff is None else _u8(cliff).reshape(-1)
         self._tmask = None if tmask is None else _u8(tmask).reshape(-1)
@@ -151,7 +172,8 @@ class Plan:
             for k, z in enumerate(m.reshape(-1)):
                 arr[i].m[2 * k] = z.real
                 arr[i].m[2 * k + 1] = z.imag
-        opts = _Opts(window_bits, bottom_bits, top_bits, 0, hbm_budget_bytes)
+        opts = _Opts(window_bits, bottom_bits, top_bits, _precision_code(precision), hbm_budget_bytes)
+        self.precision = _precision_code(precision)
         h = _vp()
         cp = None if self._cliff is None else self._cliff.ctypes.data_as(_u8p)
         tp = None if self._tmask is None else self._tmask.ctypes.data_as(_u8p)
@@ -179,7 +201,7 @@ class Plan:
         _check(_lib.tb_plan_info(self._h, ctypes.byref(inf)), "tb_plan_info")
         return {f: getattr(inf, f) for f, _ in _Info._fields_}
 
-    PASS_SHAPES = ("fwd", "rev", "top", "bot", "bot_start", "bot_end", "top_end")
+    PASS_SHAPES = ("fwd", "rev", "top", "bot", "bot_start", "bot_end", "top_end", "tensor")
 
     @property
     def schedule(self) -> list:

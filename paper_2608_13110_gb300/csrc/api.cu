@@ -15,6 +15,7 @@
 
 #include "misc_kernels.cuh"
 #include "pass_kernel.cuh"
+#include "tc_pass.cuh"
 #include "tb_plan.h"
 #include "tb_run.h"
 #include "tbsweep.h"
@@ -78,7 +79,7 @@ bool small_path(const Plan& P) { return P.h <= SMALL_H_MAX; }
 CallLayout call_layout(const Plan& P) {
     CallLayout c;
     if (small_path(P)) return c;
-    c.nslots = (int)P.passes.size() + 2;
+    c.nslots = P.n_pass_launches() + 2;
     c.scale_bytes = align_up((int64_t)c.nslots * 8, 256);
     const int64_t nchunks = (int64_t)1 << (P.h - P.k);
     c.red_blocks = (int)std::min<int64_t>(nchunks, MAX_RED_BLOCKS);
@@ -197,6 +198,33 @@ int run_device(const Plan& P, const uint8_t* d_bits, int64_t nb, void* d_ws, int
             TB_CUDA(launch_init(ip, (int)std::min<int64_t>(ip.nchunks, 8LL * nsm), st));
         }
 
+        if (P.opts.precision != TB_PRECISION_FP32) {
+            int* fault = device_fault_word();
+            if (!fault) return fail(TB_ECUDA, "device fault word not found");
+            const uint8_t* mats = static_cast<const uint8_t*>(d_ws) + L.tc_mats;
+            for (size_t k = 0; k < P.tc_passes.size(); ++k) {
+                const TcPass& d = P.tc_passes[k];
+                TcParams tp;
+                tp.B = boundary;
+                tp.b_stride = b_stride;
+                tp.h = P.h; tp.lo = d.lo; tp.n = P.n;
+                tp.tile_shift = P.h - P.tc_wb - TC_VEC_BITS;
+                tp.ntiles = (int64_t)nbat << tp.tile_shift;
+                tp.mat = mats + d.mat;
+                tp.steps = steps;
+                tp.pre = d.pre;
+                tp.post = d.post;
+                tp.bits = bits;
+                tp.maxs = maxs;
+                tp.exps = exps;
+                tp.sstride = sstride;
+                tp.slot = (int)k;
+                tp.fault = fault;
+                const int grid = (int)std::min<int64_t>(tp.ntiles, (int64_t)TC_CTAS_PER_SM * nsm);
+                ProfScope ps(PC_PASS, 16.0 * (double)nbat * (double)b_stride, st);
+                TB_CUDA(launch_tc_pass(P.opts.precision, tp, grid, st));
+            }
+        }
         for (size_t k = 0; k < P.passes.size(); ++k) {
             const PassDesc& d = P.passes[k];
             PassParams pp;
@@ -232,7 +260,7 @@ int run_device(const Plan& P, const uint8_t* d_bits, int64_t nb, void* d_ws, int
         rp.maxs = maxs;
         rp.exps = exps;
         rp.sstride = sstride;
-        rp.slot = (int)P.passes.size();
+        rp.slot = P.n_pass_launches();
         rp.partials = partials;
         {
             ProfScope ps(PC_REDUCE, 8.0 * (double)nbat * (double)b_stride, st);
@@ -310,7 +338,7 @@ int tb_plan_info(const tb_plan* plan, tb_plan_info_t* info) {
     info->log2_cost = P.log2cost;
     info->boundary_bytes = (int64_t)8 << P.h;
     info->n_steps = (int)P.steps.size();
-    info->n_passes = (int)P.passes.size();
+    info->n_passes = P.n_pass_launches();
     info->table_bytes = P.lay.total;
     return TB_OK;
 }
@@ -318,6 +346,15 @@ int tb_plan_info(const tb_plan* plan, tb_plan_info_t* info) {
 int tb_plan_schedule(const tb_plan* plan, int32_t* sched, int cap) {
     if (!plan) return -1;
     const Plan& P = plan->p;
+    if (P.opts.precision != TB_PRECISION_FP32) {
+        const int np = (int)P.tc_passes.size();
+        for (int i = 0; i < np && i < cap && sched; ++i) {
+            sched[3 * i] = P_TENSOR;
+            sched[3 * i + 1] = P.tc_wb;
+            sched[3 * i + 2] = P.tc_passes[i].lo;
+        }
+        return np;
+    }
     const int np = (int)P.passes.size();
     for (int i = 0; i < np && i < cap && sched; ++i) {
         sched[3 * i] = P.passes[i].type;
@@ -411,6 +448,18 @@ int tb_profile_end(tb_profile_t* out) {
     }
     g_prof.recs.clear();
     g_prof.used = 0;
+    return TB_OK;
+}
+
+int tb_device_faults(int32_t* count) {
+    if (!count) return fail(TB_EINVAL, "count is NULL");
+    int* w = device_fault_word();
+    if (!w) return fail(TB_ECUDA, "device fault word not found");
+    TB_CUDA(cudaDeviceSynchronize());
+    int v = 0;
+    TB_CUDA(cudaMemcpy(&v, w, sizeof(int), cudaMemcpyDeviceToHost));
+    TB_CUDA(cudaMemset(w, 0, sizeof(int)));
+    *count = v;
     return TB_OK;
 }
 

@@ -141,7 +141,7 @@ int tb_batch_create(const tb_batch_item* items, int nitems, void* d_ws, int64_t 
         if (!small_path(items[i].plan->p) && items[i].nb > 0) wide.push_back(i);
     auto cost = [&](int i) {
         const Plan& P = items[i].plan->p;
-        return (double)items[i].nb * (double)(P.passes.size() + 2) * std::ldexp(1.0, P.h);
+        return (double)items[i].nb * (double)(P.n_pass_launches() + 2) * std::ldexp(1.0, P.h);
     };
     std::sort(wide.begin(), wide.end(), [&](int a, int b) { return cost(a) > cost(b); });
     std::vector<std::vector<int>> branch(nbranches);

@@ -315,13 +315,15 @@ int plan_build(Plan& P, int n, int d, const uint8_t* cliff, const uint8_t* tmask
     auto U = [&](int q, int t) -> const M2& { return P.U[(size_t)t * n + q]; };
 
     // ---- paired steps of rows 1..n-2
-    P.steps.clear(); P.step_tgt.clear(); P.step_ctl.clear(); P.step_xq.clear(); P.row_end.clear();
+    P.steps.clear(); P.steps64.clear(); P.step_tgt.clear(); P.step_ctl.clear(); P.step_xq.clear();
+    P.row_end.clear();
     for (int r = 1; r <= n - 2; ++r) {
         const bool fwd = (r % 2) == 1;
         for (int i = 0; i < h; ++i) {
             const int p = fwd ? i : h - 1 - i;
             const bool xdep = (p == h - 1);
             StepG sg;
+            std::array<cd, 16> sg64;
             for (int x = 0; x < 2; ++x)
                 for (int c = 0; c < 2; ++c)
                     for (int ap = 0; ap < 2; ++ap)
@@ -342,8 +344,10 @@ int plan_build(Plan& P, int n, int d, const uint8_t* cliff, const uint8_t* tmask
                             if (fwd && p == h - 1) acc *= U(r, d).a[x * 2 + ap];
                             if (!fwd && p == 0) acc *= U(r, 0).a[ap * 2 + 0];
                             sg.g[x][c * 4 + ap * 2 + s] = f2(acc);
+                            sg64[x * 8 + c * 4 + ap * 2 + s] = acc;
                         }
             P.steps.push_back(sg);
+            P.steps64.push_back(sg64);
             P.step_tgt.push_back((int8_t)p);
             int ctl = -1;
             if (fwd && p > 0) ctl = p - 1;
@@ -444,7 +448,20 @@ int plan_build(Plan& P, int n, int d, const uint8_t* cliff, const uint8_t* tmask
 
     // ---- pass schedule (boundaries wider than one CTA's shared memory)
     P.passes.clear();
-    if (h > SMALL_H_MAX && n > 2) {
+    P.tc_passes.clear();
+    P.tc_mats.clear();
+    P.tc_wb = 0;
+    if (P.opts.precision != TB_PRECISION_FP32 && P.opts.precision != TB_PRECISION_TF32X3 &&
+        P.opts.precision != TB_PRECISION_BF16X3) {
+        err = "precision must be TB_PRECISION_FP32, _TF32X3 or _BF16X3";
+        return TB_EINVAL;
+    }
+    if (P.opts.precision != TB_PRECISION_FP32) {
+        if (h > SMALL_H_MAX && n > 2) {
+            const int rc = tc_schedule(P, err);
+            if (rc != TB_OK) return rc;
+        }
+    } else if (h > SMALL_H_MAX && n > 2) {
         int mmax = P.opts.window_bits ? P.opts.window_bits : MAX_WINDOW;
         if (mmax < MIN_WINDOW || mmax > MAX_WINDOW) { err = "window_bits must be in 5..10"; return TB_EINVAL; }
         const int b_lo = P.opts.bottom_bits ? P.opts.bottom_bits : MIN_WINDOW;
@@ -490,6 +507,7 @@ int plan_build(Plan& P, int n, int d, const uint8_t* cliff, const uint8_t* tmask
     L.red_low = put((int64_t)P.red_low.size() * 8);
     L.red_mid = put((int64_t)P.red_mid.size() * 8);
     L.red_top = put((int64_t)P.red_top.size() * 8);
+    L.tc_mats = put((int64_t)P.tc_mats.size());
     L.total = off;
     P.blob.assign((size_t)L.total, 0);
     auto cp = [&](int64_t o, const void* src, size_t bytes) {
@@ -506,6 +524,7 @@ int plan_build(Plan& P, int n, int d, const uint8_t* cliff, const uint8_t* tmask
     cp(L.red_low, P.red_low.data(), P.red_low.size() * 8);
     cp(L.red_mid, P.red_mid.data(), P.red_mid.size() * 8);
     cp(L.red_top, P.red_top.data(), P.red_top.size() * 8);
+    cp(L.tc_mats, P.tc_mats.data(), P.tc_mats.size());
     return TB_OK;
 }
 

@@ -48,7 +48,8 @@ enum PassType : int {
     P_BOT_START = 4,
     P_BOT_END = 5,
     P_TOP_END = 6,
-    P_NTYPES = 7
+    P_NTYPES = 7,
+    P_TENSOR = 7   // schedule code of a dense tensor-core pass
 };
 
 __host__ __device__ constexpr int pass_nsteps(int type, int M) {
@@ -73,6 +74,45 @@ struct PassDesc {
     int xs_q[2];     // the qubit whose output bit selects its variant
 };
 
+// ---- Tensor-core dense blocks (TB_PRECISION_TF32X3 / TB_PRECISION_BF16X3) --
+// A dense pass works on WB consecutive address bits [lo, lo+WB). The steps of
+// the pass whose target and control both lie in the window are composed on
+// the host into one 2^WB x 2^WB complex matrix; the device applies it to all
+// 2^(h-WB) "vectors" (fixed values of the other address bits) as a real GEMM
+// D[vector][2*j'+part'] = sum_k A[vector][k] Bm[k][2*j'+part'], k = 2*j+part,
+// on the tensor cores. A step whose control bit lies outside the window, and
+// the two steps that depend on an output bit, run as FP32 register steps
+// before (pre) or after (post) the block.
+constexpr int TC_THREADS = 128;     // one warpgroup; thread i owns TMEM lane i
+constexpr int TC_VEC_BITS = 7;      // 128 vectors per tile (one per TMEM lane)
+constexpr int TC_CTAS_PER_SM = 2;
+constexpr int TC_WB_TF32 = 5;       // 64 x 64 real block, FP32 operands
+constexpr int TC_WB_BF16 = 6;       // 128 x 128 real block, 16-bit operands
+constexpr int TC_MAX_WB = 6;
+
+// A register step around a dense block.
+struct TcStep {
+    int t;      // window-relative target bit; -1: no step
+    int cmode;  // 0: no control; 1: control = address bit cbit (outside the
+                // window, fixed per vector); 2: control = window bit cbit
+    int cbit;
+    int step;   // index into the plan's step array
+    int xq;     // qubit whose output bit selects the variant, -1: none
+};
+
+struct TcPass {
+    int lo;        // address bit of window bit 0
+    TcStep pre, post;
+    int64_t mat;   // byte offset of the pass's split matrix in the tc_mats table
+    int step0;     // contiguous steps covered (pre, block, post)
+    int nsteps;
+};
+
+// Bytes of one split matrix (hi then lo) of a dense block over WB bits.
+__host__ __device__ constexpr int64_t tc_mat_bytes(int WB, int elem_bytes) {
+    return 2LL * (2LL << WB) * (2LL << WB) * elem_bytes;
+}
+
 // Byte offsets of the device tables inside the workspace head.
 struct TableLayout {
     int64_t steps;     // StepG[n_steps]
@@ -86,6 +126,7 @@ struct TableLayout {
     int64_t red_low;   // float2[2^k][2]       last row: column vectors
     int64_t red_mid;   // float2[2^m][4]       last row: 2x2 matrices
     int64_t red_top;   // float2[2][2^top][2]  last row: [x] row vectors
+    int64_t tc_mats;   // split dense-block matrices of the tensor-core passes
     int64_t total;
 };
 

@@ -1,6 +1,7 @@
 // Host-side plan object of the temporal-boundary sweep.
 #pragma once
 
+#include <array>
 #include <complex>
 #include <string>
 #include <vector>
@@ -24,12 +25,20 @@ struct Plan {
     std::vector<M2> U;  // (d+1)*n folded slot gates, index t*n + q
     // paired steps of rows 1..n-2 in execution order
     std::vector<StepG> steps;
+    std::vector<std::array<std::complex<double>, 16>> steps64;  // the same in FP64
     std::vector<int8_t> step_tgt, step_ctl;
     std::vector<int16_t> step_xq;
     std::vector<int32_t> row_end;
     // pass schedule (empty when the boundary fits one CTA)
     std::vector<PassDesc> passes;
     std::vector<int> windows;
+    // dense tensor-core schedule (precision TF32X3 / BF16X3)
+    std::vector<TcPass> tc_passes;
+    std::vector<uint8_t> tc_mats;
+    int tc_wb = 0;
+    int n_pass_launches() const {
+        return opts.precision != TB_PRECISION_FP32 ? (int)tc_passes.size() : (int)passes.size();
+    }
     // row-0 and last-row tables
     int k = 0, m = 0, top = 0;
     std::vector<float2> init_low, init_mid, init_top, red_low, red_mid, red_top;
@@ -42,6 +51,9 @@ struct Plan {
 };
 
 uint64_t next_plan_uid();
+
+// Build the dense tensor-core schedule and its split matrices (tc_plan.cpp).
+int tc_schedule(Plan& P, std::string& err);
 
 int plan_build(Plan& P, int n, int d, const uint8_t* cliff, const uint8_t* tmask,
                const tb_gate1q* extra, int n_extra, const tb_opts* opts, std::string& err);

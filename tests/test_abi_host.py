@@ -164,4 +164,38 @@ def test_pass_cases_cover_every_shape(tb):
     seen = set()
     for n, d, wb, bb, tt in mod.PASS_CASES:
         seen |= {(s, m) for s, m, _ in tb.Plan(n, d, window_bits=wb, bottom_bits=bb, top_bits=tt).schedule}
-    assert seen == {(s, m) for s in tb.Plan.PASS_SHAPES for m in range(5, 11)}
+    assert seen == {(s, m) for s in tb.Plan.PASS_SHAPES if s != "tensor" for m in range(5, 11)}
+
+
+# ------------------------------------------------ split-precision tensor-core schedule
+
+@pytest.mark.parametrize("prec,wb", [("tf32x3", 5), ("bf16x3", 6)])
+def test_dense_schedule_shape(tb, prec, wb):
+    """Every dense pass spans WB address bits inside the boundary; rows are
+    cut into ceil((h - WB) / WB) + 1 chunks each, the first (forward) chunk
+    of a row sharing the pass at address bit 0 with the previous row's last."""
+    for n in (3, 4, 5, 8, 13):
+        for d in range(26, 67, 2):
+            h = d // 2
+            p = tb.Plan(n, d, precision=prec)
+            sched = p.schedule
+            assert len(sched) == p.info["n_passes"] > 0
+            assert all(s == "tensor" and m == wb and 0 <= lo <= h - wb for s, m, lo in sched)
+            per_row = -(-(h - wb) // wb) + 1
+            rows = n - 2
+            assert len(sched) == rows * per_row - (rows - 1) // 2
+            assert sched[0][2] == 0
+
+
+def test_dense_schedule_options(tb):
+    with pytest.raises(tb.TbError) as e:
+        tb.Plan(8, 30, precision=3)
+    assert e.value.status == tb.TB_EINVAL
+    with pytest.raises(ValueError):
+        tb.Plan(8, 30, precision="fp16")
+    # narrow boundaries keep the single-CTA kernel: no HBM passes
+    assert tb.Plan(12, 24, precision="bf16x3").info["n_passes"] == 0
+    # dense matrices (hi and lo) are part of the plan's device tables
+    base = tb.Plan(70, 64).info["table_bytes"]
+    assert tb.Plan(70, 64, precision="bf16x3").info["table_bytes"] >= base + 375 * 2 * 128 * 128 * 2
+    assert tb.Plan(70, 64, precision="tf32x3").info["table_bytes"] >= base + 443 * 2 * 64 * 64 * 4
