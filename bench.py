@@ -207,7 +207,7 @@ def run_ours(args, rank, world, local):
         c = W.random_circuit(n_, d_, None, nb, 4000 + 100 * rank + d_)
     else:
         c = W.precision_70_64(replica=rank, nb=nb)
-    plan = tb.Plan.from_circuit(c)
+    plan = tb.Plan.from_circuit(c, precision=args.precision)
     info = plan.info
     h = info["boundary_bits"]
     ws = torch.empty(plan.workspace_bytes(nb), dtype=torch.uint8, device=dev)
@@ -266,13 +266,14 @@ def run_ours(args, rank, world, local):
     p = prof["pass"]
     achieved = p["bytes"] / (p["ms"] / 1e3) / 1e9 if p["ms"] > 0 else None
     n_launch = sum(v["launches"] for v in prof.values())
-    traffic = pass_traffic(h)
+    traffic = pass_traffic(h) if args.precision == "fp32" else None
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_dev_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "complex64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": 70, "d": 64, "n_t": 426, "bitstrings_per_step": nb,
+                   "pass_arithmetic": args.precision,
                    "width": info["width"], "passes_per_amplitude": info["n_passes"],
                    "l2": "inputs larger than L2 (32 GiB boundary, 129 MB L2)",
                    "parallelism": f"replicas x{world}"},
@@ -281,7 +282,8 @@ def run_ours(args, rank, world, local):
         "gpu_launches": n_launch,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": (achieved / hbm_peak) if achieved else None, "traffic": traffic,
-                     "kernel": "pass_kernel", "peak_source": f"{peak_src} copy bandwidth",
+                     "kernel": "pass_kernel" if args.precision == "fp32" else "tc_pass_kernel",
+                     "peak_source": f"{peak_src} copy bandwidth",
                      "pass_launches": p["launches"], "pass_ms_total": p["ms"],
                      "pass_share_of_kernel_time": p["ms"] / max(1e-9, sum(v["ms"] for v in prof.values()))},
         "clocks": clk,
@@ -358,6 +360,99 @@ def run_batch_workload(args, rank, world, local):
             "plain": {"value": world * namps * args.steps / t_p, "unit": UNIT, "ms_per_step": 1e3 * t_p / args.steps,
                       "how": "one tb_amplitudes_device call per circuit, back to back on one stream"},
             "identical_to_plain": bool(same), "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def _golden(name):
+    """Stored FP64 amplitudes (written by the scripts in tests/golden from the
+    oracle) with their circuit, or None if absent."""
+    path = os.path.join(ROOT, "tests", "golden", name)
+    if not os.path.exists(path):
+        return None
+    g = json.load(open(path))
+    c = W.Circuit(g["n"], g["d"], np.array(g["cliff"], np.uint8), np.array(g["tmask"], np.uint8),
+                  np.array(g["bits"], np.uint8), 0)
+    return c, np.array([complex(a, b) for a, b in g["amps"]])
+
+
+def _errors(got, ref):
+    rel = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-300)
+    return {"rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)), "max_rel": float(rel.max()),
+            "n_amplitudes": int(ref.size)}
+
+
+def run_precision_workload(args, rank, world, local):
+    """The plain complex64 path (FP32 FMA staircase) against the split-precision
+    tensor-core forms (3xTF32 and 3xBF16 dense blocks) on the n=70, d=64
+    workload: amplitudes/s, the pass kernels' HBM GB/s, and each form's error
+    against stored FP64 values (n=32, d=48 naive-boundary oracle; n=70, d=64
+    closed form), all on the same GPU in the same run."""
+    import torch
+    import paper_2608_13110_gb300 as tb
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    nb = args.nb_precision
+    c = W.precision_70_64(replica=rank, nb=nb)
+    stream = torch.cuda.current_stream(dev)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm_peak = peaks.get("hbm_gbs") or 6800.0
+    goldens = {"n32_d48_fp64_oracle": _golden("precision_n32_d48.json"),
+               "n70_d64_closed_form": _golden("closed_form_n70_d64.json")}
+    forms = {}
+    ref_amps = None
+    clocks = ClockSampler(local)
+    for form in ("fp32", "tf32x3", "bf16x3"):
+        plan = tb.Plan.from_circuit(c, precision=form)
+        ws = torch.empty(plan.workspace_bytes(nb), dtype=torch.uint8, device=dev)
+        plan.upload(ws, stream)
+        d_bits = torch.from_numpy(c.bits).to(dev)
+        d_out = torch.empty((nb, 2), dtype=torch.float64, device=dev)
+        for _ in range(args.warmup):
+            plan.amplitudes_device(d_bits, ws, d_out, stream)
+        torch.cuda.synchronize(dev)
+        barrier(world, dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        tb.profile_begin()
+        e0.record(stream)
+        for _ in range(args.steps):
+            plan.amplitudes_device(d_bits, ws, d_out, stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        prof = tb.profile_end()
+        t = max_over_ranks(e0.elapsed_time(e1) / 1e3, world, dev)
+        amps = d_out.cpu().numpy().view(np.complex128).reshape(-1)
+        del ws
+        if ref_amps is None:
+            ref_amps = amps
+        p = prof["pass"]
+        achieved = p["bytes"] / (p["ms"] / 1e3) / 1e9
+        f = {"amps_per_s": world * nb * args.steps / t, "ms_per_step": 1e3 * t / args.steps,
+             "passes_per_amplitude": plan.info["n_passes"],
+             "pass_kernel": {"achieved_gbs": achieved, "frac_of_measured_hbm": achieved / hbm_peak,
+                             "avg_ms": p["ms"] / max(1, p["launches"])},
+             "rel_l2_vs_fp32_n70_d64": float(np.linalg.norm(amps - ref_amps) / np.linalg.norm(ref_amps)),
+             "errors_vs_fp64": {}}
+        for name, g in goldens.items():
+            if g is None:
+                continue
+            gc, gref = g
+            got = tb.Plan.from_circuit(gc, precision=form).amplitudes(gc.bits)
+            f["errors_vs_fp64"][name] = _errors(got, gref)
+        f["device_faults"] = tb.device_faults()
+        forms[form] = f
+    clk = clocks.stop()
+    line = {"metric": "amplitudes/s by pass arithmetic (n=70, d=64) with error vs FP64",
+            "value": forms["fp32"]["amps_per_s"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": forms["fp32"]["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "complex64", "data": "synthetic",
+            "config": {"workload": f"brickwork CZ n=70 d=64, random Cliffords, 426 T, {nb} bitstrings/step, "
+                                   "width 32; value = the plain FP32 form",
+                       "l2": "inputs larger than L2 (32 GiB boundary)", "parallelism": f"replicas x{world}",
+                       "peak_hbm_gbs": hbm_peak},
+            "forms": forms, "clocks": clk}
     if rank == 0:
         print(json.dumps(line))
 
@@ -442,9 +537,13 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="n70d64", choices=("n70d64", "batch", "serve"),
+    ap.add_argument("--workload", default="n70d64", choices=("n70d64", "batch", "serve", "precision"),
                     help="n70d64: the headline metric; batch: 64 uneven circuits in one graph; "
-                         "serve: Poisson request stream through the serving runtime")
+                         "serve: Poisson request stream through the serving runtime; "
+                         "precision: FP32 vs 3xTF32 / 3xBF16 tensor-core passes with errors vs FP64")
+    ap.add_argument("--precision", default="fp32", choices=("fp32", "tf32x3", "bf16x3"),
+                    help="pass arithmetic of the n70d64 workload")
+    ap.add_argument("--nb-precision", type=int, default=4, help="bitstrings per step in the precision workload")
     ap.add_argument("--requests", type=int, default=200, help="requests in the serve workload")
     ap.add_argument("--shape", default="", help="n,d of a smaller circuit (profiling only; not the reported workload)")
     args = ap.parse_args()
@@ -457,6 +556,8 @@ def main():
             run_batch_workload(args, rank, world, local)
         elif args.workload == "serve":
             run_serve_workload(args, rank, world, local)
+        elif args.workload == "precision":
+            run_precision_workload(args, rank, world, local)
         else:
             run_ours(args, rank, world, local)
     if _env_int("WORLD_SIZE", 1) > 1:
