@@ -77,6 +77,65 @@ int64_t canon_offset(int nn, int kk, int K, int eb) {
     return ((int64_t)(nn / 8) * (K / T) + kk / T) * 128 + (nn % 8) * 16 + (kk % T) * eb;
 }
 
+// Compose the steps (plan indices, in order) acting on address bits
+// [base, base + WB) into one dense complex block in FP64, embed it as the real
+// (2^(WB+1))^2 operand (k = 2*j + part_in, nn = 2*j' + part_out), split it into
+// hi + lo parts of the operand type and store both at dst (hi, then lo) in the
+// K-major canonical layout.
+bool compose_block(const Plan& P, const std::vector<int>& steps, int base, int WB, bool tf32, uint8_t* dst,
+                   std::string& err) {
+    const int NV = 1 << WB, K = 2 * NV, eb = tf32 ? 4 : 2;
+    std::vector<cd> Mt((size_t)NV * NV), v(NV), w(NV);
+    for (int ji = 0; ji < NV; ++ji) {
+        std::fill(v.begin(), v.end(), cd(0.0));
+        v[ji] = 1.0;
+        for (const int s : steps) {
+            const int t = P.step_tgt[s] - base;
+            const int ctl = P.step_ctl[s];
+            const int cb = ctl < 0 ? -1 : ctl - base;
+            if (t < 0 || t >= WB || (ctl >= 0 && (cb < 0 || cb >= WB)) || P.step_xq[s] >= 0) {
+                err = "internal: dense block step leaves its window";
+                return false;
+            }
+            const auto& g = P.steps64[s];  // variant x = 0 (the step does not depend on x)
+            for (int j = 0; j < NV; ++j) {
+                if ((j >> t) & 1) continue;
+                const int cv = cb < 0 ? 0 : (j >> cb) & 1;
+                const cd v0 = v[j], v1 = v[j | (1 << t)];
+                w[j] = g[cv * 4 + 0] * v0 + g[cv * 4 + 1] * v1;
+                w[j | (1 << t)] = g[cv * 4 + 2] * v0 + g[cv * 4 + 3] * v1;
+            }
+            v.swap(w);
+        }
+        for (int jo = 0; jo < NV; ++jo) Mt[(size_t)jo * NV + ji] = v[jo];
+    }
+    uint8_t* hi = dst;
+    uint8_t* lo = dst + tc_mat_bytes(WB, eb) / 2;
+    for (int nn = 0; nn < K; ++nn)
+        for (int k = 0; k < K; ++k) {
+            const cd z = Mt[(size_t)(nn >> 1) * NV + (k >> 1)];
+            const int po = nn & 1, pi = k & 1;
+            const double val = po == 0 ? (pi == 0 ? z.real() : -z.imag()) : (pi == 0 ? z.imag() : z.real());
+            const int64_t off = canon_offset(nn, k, K, eb);
+            if (tf32) {
+                const float vh = round_tf32(val);
+                const float vl = round_tf32(val - (double)vh);
+                std::memcpy(hi + off, &vh, 4);
+                std::memcpy(lo + off, &vl, 4);
+            } else {
+                const float vh = round_bf16(val);
+                const float vl = round_bf16(val - (double)vh);
+                uint32_t uh, ul;
+                std::memcpy(&uh, &vh, 4);
+                std::memcpy(&ul, &vl, 4);
+                const uint16_t bh = (uint16_t)(uh >> 16), bl = (uint16_t)(ul >> 16);
+                std::memcpy(hi + off, &bh, 2);
+                std::memcpy(lo + off, &bl, 2);
+            }
+        }
+    return true;
+}
+
 }  // namespace
 
 int tc_schedule(Plan& P, std::string& err) {
@@ -140,13 +199,10 @@ int tc_schedule(Plan& P, std::string& err) {
     }
 
     // ---- classify the steps of each chunk, compose the dense block
-    const int NV = 1 << WB;        // complex entries per vector
-    const int K = 2 * NV;          // real GEMM dimension
     const int64_t mat_bytes = tc_mat_bytes(WB, eb);
     P.tc_passes.clear();
     P.tc_mats.assign((size_t)(mat_bytes * (int64_t)chunks.size()), 0);
     int expect = 0;
-    std::vector<cd> Mt((size_t)NV * NV), v(NV), w(NV);
     for (size_t ci = 0; ci < chunks.size(); ++ci) {
         const Chunk& c = chunks[ci];
         TcPass tp;
@@ -193,57 +249,8 @@ int tc_schedule(Plan& P, std::string& err) {
             err = "internal: unsupported post-step";
             return TB_EINVAL;
         }
-        // composed block: columns are images of the basis vectors
-        for (int ji = 0; ji < NV; ++ji) {
-            std::fill(v.begin(), v.end(), cd(0.0));
-            v[ji] = 1.0;
-            for (int i = first; i < last; ++i) {
-                const int s = c.steps[i];
-                const int t = P.step_tgt[s] - c.lo;
-                const int ctl = P.step_ctl[s];
-                if (t < 0 || t >= WB || (ctl >= 0 && !in_win(ctl)) || P.step_xq[s] >= 0) {
-                    err = "internal: dense block step leaves its window";
-                    return TB_EINVAL;
-                }
-                const int cb = ctl < 0 ? -1 : ctl - c.lo;
-                const auto& g = P.steps64[s];  // variant x = 0 (the step does not depend on x)
-                for (int j = 0; j < NV; ++j) {
-                    if ((j >> t) & 1) continue;
-                    const int cv = cb < 0 ? 0 : (j >> cb) & 1;
-                    const cd v0 = v[j], v1 = v[j | (1 << t)];
-                    w[j] = g[cv * 4 + 0] * v0 + g[cv * 4 + 1] * v1;
-                    w[j | (1 << t)] = g[cv * 4 + 2] * v0 + g[cv * 4 + 3] * v1;
-                }
-                v.swap(w);
-            }
-            for (int jo = 0; jo < NV; ++jo) Mt[(size_t)jo * NV + ji] = v[jo];
-        }
-        // real embedding Bm[k][nn], k = 2*ji + part_in, nn = 2*jo + part_out,
-        // split into hi + lo, stored as the K-major operand (rows nn)
-        uint8_t* hi = P.tc_mats.data() + tp.mat;
-        uint8_t* lo = hi + mat_bytes / 2;
-        for (int nn = 0; nn < K; ++nn)
-            for (int k = 0; k < K; ++k) {
-                const cd z = Mt[(size_t)(nn >> 1) * NV + (k >> 1)];
-                const int po = nn & 1, pi = k & 1;
-                const double val = po == 0 ? (pi == 0 ? z.real() : -z.imag()) : (pi == 0 ? z.imag() : z.real());
-                const int64_t off = canon_offset(nn, k, K, eb);
-                if (tf32) {
-                    const float vh = round_tf32(val);
-                    const float vl = round_tf32(val - (double)vh);
-                    std::memcpy(hi + off, &vh, 4);
-                    std::memcpy(lo + off, &vl, 4);
-                } else {
-                    const float vh = round_bf16(val);
-                    const float vl = round_bf16(val - (double)vh);
-                    uint32_t uh, ul;
-                    std::memcpy(&uh, &vh, 4);
-                    std::memcpy(&ul, &vl, 4);
-                    const uint16_t bh = (uint16_t)(uh >> 16), bl = (uint16_t)(ul >> 16);
-                    std::memcpy(hi + off, &bh, 2);
-                    std::memcpy(lo + off, &bl, 2);
-                }
-            }
+        const std::vector<int> blk(c.steps.begin() + first, c.steps.begin() + last);
+        if (!compose_block(P, blk, c.lo, WB, tf32, P.tc_mats.data() + tp.mat, err)) return TB_EINVAL;
         P.tc_passes.push_back(tp);
     }
     if (expect != (int)P.steps.size()) {
