@@ -106,6 +106,9 @@ typedef struct {
     int32_t n_passes;       /* HBM passes over the boundary per amplitude
                                (0 when the whole boundary fits one CTA) */
     int64_t table_bytes;    /* device bytes of the plan's tables */
+    int32_t open_k;         /* open output bits of an open plan, 0 otherwise */
+    int32_t open_width;     /* open plans: width of Algorithm 2's path,
+                               max(h, 2k) (Proposition 2: h for k <= d/4) */
 } tb_plan_info_t;
 
 /* Create a plan (host only: no CUDA call is made).
@@ -124,6 +127,37 @@ typedef struct {
 TB_API int tb_plan_create(int n, int d, const uint8_t* cliff, const uint8_t* tmask,
                    const tb_gate1q* extra, int n_extra, const tb_opts* opts,
                    tb_plan** out);
+
+/* Create an open plan: the output bits of the last k qubits stay open and
+ * one evaluation returns all 2^k amplitudes <a,b|U|0^n> sharing the prefix a
+ * (Algorithm 2, Sec. 4 "Constructive path for batched sampling"): the sweep of
+ * Algorithm 1 absorbs rows 0..n-k-1 (the fixed region), the early region (the
+ * open band's first 2k CZ layers) is contracted on the host in FP64 into a
+ * 2^k x 2^k matrix and joined with the boundary over the k shared bits on the
+ * device, then the late region is absorbed layer by layer, each crossing CZ
+ * with row n-k-1 contracting one boundary bit.
+ *   k: 1 <= k <= min(floor(d/4), 10, n-1) (else TB_EDOMAIN); ceil(d/2) >= 13.
+ * Other arguments as tb_plan_create. Evaluate with tb_amplitudes /
+ * tb_amplitudes_device, where a row of the input is the prefix
+ * a = (x_0..x_(n-k-1)) (n-k bytes) and the output holds 2^k amplitudes per
+ * prefix, index y = sum_j b_j 2^j with b_j the output bit of qubit n-k+j. The
+ * workspace holds one boundary and half a boundary per prefix evaluated
+ * concurrently (tb_workspace_bytes accounts for it). tb_amplitudes_noalloc,
+ * batches and servers reject open plans (TB_EINVAL). */
+TB_API int tb_plan_create_open(int n, int d, const uint8_t* cliff, const uint8_t* tmask,
+                               const tb_gate1q* extra, int n_extra, const tb_opts* opts, int k,
+                               tb_plan** out);
+
+/* Batched sampling from open-plan amplitudes (Sec. 4, "Batched sampling"):
+ * for each of na prefixes with amplitudes amps[a*2^k .. (a+1)*2^k) ((re, im)
+ * pairs, host FP64), Q_a = sum_b |amp|^2 and the suffix b drawn from
+ * p(b | a) = |amp(a, b)|^2 / Q_a by inverting its distribution function at the
+ * uniform variate u[a] in [0, 1) (the smallest b whose cumulative mass exceeds
+ * u[a] Q_a; the random numbers are inputs). Writes b[a] and, if q is not NULL,
+ * q[a] = Q_a. Host only. Returns TB_EINVAL for NULL pointers, k outside 0..30 or
+ * u outside [0, 1). */
+TB_API int tb_batched_sample(const double* amps, int k, int64_t na, const double* u, int32_t* b,
+                             double* q);
 
 /* Fill *info. */
 TB_API int tb_plan_info(const tb_plan* plan, tb_plan_info_t* info);
@@ -264,13 +298,16 @@ TB_API void tb_server_destroy(tb_server* server);
 /* Kernel timing (tracing aid). While enabled, every kernel this library
  * launches is bracketed by CUDA events on its stream. Classes: 0 boundary
  * passes, 1 row-0 writer, 2 last-row reduction, 3 finalisation, 4 narrow
- * (whole boundary in shared memory). bytes[c] is the algorithmic HBM traffic
- * of those launches: a pass reads and writes every boundary entry once
- * (16 bytes per entry), the writer writes 8, the reduction reads 8. */
+ * (whole boundary in shared memory), 5 open-plan join, 6 open-plan late
+ * crossings. bytes[c] is the algorithmic HBM traffic of those launches: a
+ * pass or a join reads and writes every boundary entry once (16 bytes per
+ * entry), the writer writes 8, the reduction reads 8, a late crossing reads
+ * two entries and writes one (24 bytes per output entry). */
+#define TB_PROFILE_CLASSES 7
 typedef struct {
-    int64_t launches[5];
-    double ms[5];
-    double bytes[5];
+    int64_t launches[TB_PROFILE_CLASSES];
+    double ms[TB_PROFILE_CLASSES];
+    double bytes[TB_PROFILE_CLASSES];
 } tb_profile_t;
 
 /* Start recording (clears earlier records). Process-wide; not reentrant. */

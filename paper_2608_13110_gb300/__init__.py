@@ -38,7 +38,8 @@ class _Info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("d", ctypes.c_int32), ("width", ctypes.c_int32),
                 ("boundary_bits", ctypes.c_int32), ("log2_cost", ctypes.c_double),
                 ("boundary_bytes", ctypes.c_int64), ("n_steps", ctypes.c_int32),
-                ("n_passes", ctypes.c_int32), ("table_bytes", ctypes.c_int64)]
+                ("n_passes", ctypes.c_int32), ("table_bytes", ctypes.c_int64),
+                ("open_k", ctypes.c_int32), ("open_width", ctypes.c_int32)]
 
 
 _vp = ctypes.c_void_p
@@ -73,6 +74,11 @@ _sig = {
     "tb_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "tb_last_error": (ctypes.c_char_p, []),
     "tb_device_faults": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32)]),
+    "tb_plan_create_open": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _u8p, _u8p, ctypes.POINTER(_Gate1q),
+                                           ctypes.c_int, ctypes.POINTER(_Opts), ctypes.c_int,
+                                           ctypes.POINTER(_vp)]),
+    "tb_batched_sample": (ctypes.c_int, [_dp, ctypes.c_int, ctypes.c_int64, _dp,
+                                         ctypes.POINTER(ctypes.c_int32), _dp]),
 }
 
 class _Lib:
@@ -141,6 +147,28 @@ def _precision_code(p) -> int:
     return int(p)
 
 
+def batched_sample(amps, u):
+    """Batched sampling (Sec. 4): amps (na, 2^k) complex from an open plan and
+    uniform variates u (na,) in [0, 1) -> (suffix indices b (na,), Q_a (na,))."""
+    a = np.ascontiguousarray(np.asarray(amps, np.complex128))
+    if a.ndim == 1:
+        a = a.reshape(1, -1)
+    na, B = a.shape
+    k = int(B).bit_length() - 1
+    if 1 << k != B:
+        raise ValueError("rows must hold 2^k amplitudes")
+    uu = np.ascontiguousarray(np.asarray(u, np.float64).reshape(-1))
+    if uu.size != na:
+        raise ValueError("one uniform variate per prefix")
+    b = np.empty(na, np.int32)
+    q = np.empty(na, np.float64)
+    av = a.view(np.float64)
+    _check(_lib.tb_batched_sample(av.ctypes.data_as(_dp), k, na, uu.ctypes.data_as(_dp),
+                                  b.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), q.ctypes.data_as(_dp)),
+           "tb_batched_sample")
+    return b, q
+
+
 def device_faults() -> int:
     """Bounded device waits that gave up since the last call (and clear)."""
     c = ctypes.c_int32()
@@ -156,7 +184,7 @@ class Plan:
 
     def __init__(self, n: int, d: int, cliff=None, tmask=None, extra=None, *,
                  window_bits: int = 0, bottom_bits: int = 0, top_bits: int = 0,
-                 hbm_budget_bytes: int = 0, precision=0):
+                 hbm_budget_bytes: int = 0, precision=0, open_k: int = 0):
         self.n, self.d = int(n), int(d)
         self._cliff = None if cliff is None else _u8(cliff).reshape(-1)
         self._tmask = None if tmask is None else _u8(tmask).reshape(-1)
@@ -177,8 +205,14 @@ class Plan:
         h = _vp()
         cp = None if self._cliff is None else self._cliff.ctypes.data_as(_u8p)
         tp = None if self._tmask is None else self._tmask.ctypes.data_as(_u8p)
-        _check(_lib.tb_plan_create(self.n, self.d, cp, tp, arr if ex else None, len(ex),
-                                   ctypes.byref(opts), ctypes.byref(h)), "tb_plan_create")
+        self.open_k = int(open_k)
+        if self.open_k:
+            _check(_lib.tb_plan_create_open(self.n, self.d, cp, tp, arr if ex else None, len(ex),
+                                            ctypes.byref(opts), self.open_k, ctypes.byref(h)),
+                   "tb_plan_create_open")
+        else:
+            _check(_lib.tb_plan_create(self.n, self.d, cp, tp, arr if ex else None, len(ex),
+                                       ctypes.byref(opts), ctypes.byref(h)), "tb_plan_create")
         self._h = h
 
     @classmethod
@@ -231,7 +265,7 @@ class Plan:
     def amplitudes_device(self, d_bits, ws, d_out, stream=None) -> None:
         """Enqueue the sweep: d_bits (nb, n) uint8 and d_out (nb, 2) float64 are
         CUDA tensors; ``ws`` must hold this plan's tables (``upload``)."""
-        nb = d_bits.shape[0] if d_bits.dim() > 1 else d_bits.numel() // self.n
+        nb = d_bits.shape[0] if d_bits.dim() > 1 else d_bits.numel() // self.row_bytes
         _check(_lib.tb_amplitudes_device(self._h, d_bits.data_ptr(), nb, ws.data_ptr(), ws.numel(),
                                          d_out.data_ptr(), _stream_handle(stream)),
                "tb_amplitudes_device")
@@ -244,19 +278,29 @@ class Plan:
         _check(_lib.tb_amplitudes_noalloc(self._h, d_bits.data_ptr(), nb, d_out.data_ptr(),
                                           _stream_handle(stream)), "tb_amplitudes_noalloc")
 
+    @property
+    def row_bytes(self) -> int:
+        """Bytes of one input row: a bitstring (n), or an open plan's prefix (n - k)."""
+        return self.n - self.open_k
+
     def amplitudes(self, bits, ws=None, stream=None, out=None) -> np.ndarray:
-        """Host bitstrings (nb, n) -> host complex128 amplitudes; synchronous."""
+        """Host bitstrings (nb, n) -> host complex128 amplitudes (nb,);
+        synchronous. For an open plan the rows are prefixes (nb, n - k) and
+        the result is (nb, 2^k): entry [i, y] = <a_i, b|U|0^n>,
+        y = sum_j b_j 2^j."""
         b = _u8(bits)
         if b.ndim == 1:
             b = b.reshape(1, -1)
         nb = b.shape[0]
+        na = 1 << self.open_k
         if out is None:
-            out = np.empty((nb, 2), np.float64)
+            out = np.empty((nb * na, 2), np.float64)
         if ws is None:
             ws = self.alloc_workspace(nb)
         _check(_lib.tb_amplitudes(self._h, b.ctypes.data_as(_u8p), nb, ws.data_ptr(), ws.numel(),
                                   out.ctypes.data_as(_dp), _stream_handle(stream)), "tb_amplitudes")
-        return out.view(np.complex128).reshape(-1)
+        z = out.view(np.complex128).reshape(-1)
+        return z.reshape(nb, na) if self.open_k else z
 
 
 class _BatchItem(ctypes.Structure):
@@ -368,11 +412,11 @@ class Server:
 
 
 class _Profile(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_int64 * 5), ("ms", ctypes.c_double * 5),
-                ("bytes", ctypes.c_double * 5)]
+    _fields_ = [("launches", ctypes.c_int64 * 7), ("ms", ctypes.c_double * 7),
+                ("bytes", ctypes.c_double * 7)]
 
 
-PROFILE_CLASSES = ("pass", "init", "reduce", "finalize", "narrow")
+PROFILE_CLASSES = ("pass", "init", "reduce", "finalize", "narrow", "join", "late")
 
 
 def profile_begin() -> None:

@@ -16,6 +16,7 @@
 #include "misc_kernels.cuh"
 #include "pass_kernel.cuh"
 #include "tc_pass.cuh"
+#include "open_kernels.cuh"
 #include "tb_plan.h"
 #include "tb_run.h"
 #include "tbsweep.h"
@@ -31,7 +32,8 @@ int fail(int code, const std::string& msg) {
 }
 
 // ---- optional per-launch timing -------------------------------------------
-enum { PC_PASS = 0, PC_INIT = 1, PC_REDUCE = 2, PC_FINAL = 3, PC_SMALL = 4, PC_N = 5 };
+enum { PC_PASS = 0, PC_INIT = 1, PC_REDUCE = 2, PC_FINAL = 3, PC_SMALL = 4, PC_JOIN = 5, PC_LATE = 6, PC_N = 7 };
+static_assert(PC_N == TB_PROFILE_CLASSES, "profile classes");
 
 struct Profiler {
     std::mutex mu;
@@ -83,14 +85,15 @@ CallLayout call_layout(const Plan& P) {
     c.scale_bytes = align_up((int64_t)c.nslots * 8, 256);
     const int64_t nchunks = (int64_t)1 << (P.h - P.k);
     c.red_blocks = (int)std::min<int64_t>(nchunks, MAX_RED_BLOCKS);
-    c.partial_bytes = align_up((int64_t)c.red_blocks * 16, 256);
+    c.partial_bytes = P.open_k ? 0 : align_up((int64_t)c.red_blocks * 16, 256);
     c.boundary_bytes = (int64_t)8 << P.h;
-    c.per_b = c.scale_bytes + c.partial_bytes + c.boundary_bytes;
+    c.half_bytes = P.open_k ? ((int64_t)8 << (P.h - 1)) : 0;
+    c.per_b = c.scale_bytes + c.partial_bytes + c.boundary_bytes + c.half_bytes;
     return c;
 }
 
 int64_t staging_bytes(const Plan& P, int64_t nb) {
-    return align_up(nb * P.n, 256) + align_up(nb * 16, 256);
+    return align_up(nb * in_row(P), 256) + align_up(nb * 16 * amps_per_row(P), 256);
 }
 
 int64_t max_batch(const Plan& P, const CallLayout& c) {
@@ -175,16 +178,17 @@ int run_device(const Plan& P, const uint8_t* d_bits, int64_t nb, void* d_ws, int
     const int64_t b_stride = (int64_t)1 << P.h;
     const int nsm = num_sms();
     const StepG* steps = tab<StepG>(d_ws, L.steps);
+    const int xstride = (int)in_row(P);  // bytes between the input rows of two batch elements
 
     for (int64_t b0 = 0; b0 < nb; b0 += batch) {
         const int nbat = (int)std::min<int64_t>(batch, nb - b0);
-        const uint8_t* bits = d_bits + b0 * P.n;
+        const uint8_t* bits = d_bits + b0 * xstride;
         TB_CUDA(cudaMemsetAsync(scales, 0, (size_t)(nbat * c.scale_bytes), st));
 
         InitParams ip;
         ip.B = boundary;
         ip.b_stride = b_stride;
-        ip.h = P.h; ip.k = P.k; ip.m = P.m; ip.top = P.top; ip.n = P.n;
+        ip.h = P.h; ip.k = P.k; ip.m = P.m; ip.top = P.top; ip.n = xstride;
         ip.chunk_shift = P.h - P.k;
         ip.nchunks = (int64_t)nbat << ip.chunk_shift;
         ip.bits = bits;
@@ -207,7 +211,7 @@ int run_device(const Plan& P, const uint8_t* d_bits, int64_t nb, void* d_ws, int
                 TcParams tp;
                 tp.B = boundary;
                 tp.b_stride = b_stride;
-                tp.h = P.h; tp.lo = d.lo; tp.n = P.n;
+                tp.h = P.h; tp.lo = d.lo; tp.n = xstride;
                 tp.tile_shift = P.h - P.tc_wb - TC_VEC_BITS;
                 tp.ntiles = (int64_t)nbat << tp.tile_shift;
                 tp.mat = mats + d.mat;
@@ -230,7 +234,7 @@ int run_device(const Plan& P, const uint8_t* d_bits, int64_t nb, void* d_ws, int
             PassParams pp;
             pp.B = boundary;
             pp.b_stride = b_stride;
-            pp.h = P.h; pp.lo = d.lo; pp.n = P.n;
+            pp.h = P.h; pp.lo = d.lo; pp.n = xstride;
             pp.tile_shift = P.h - TILE_BITS;
             pp.ntiles = (int64_t)nbat << pp.tile_shift;
             pp.steps = steps + d.step0;
@@ -244,6 +248,55 @@ int run_device(const Plan& P, const uint8_t* d_bits, int64_t nb, void* d_ws, int
             const int grid = (int)std::min<int64_t>(pp.ntiles, (int64_t)PASS_CTAS_PER_SM * nsm);  // persistent CTAs
             ProfScope ps(PC_PASS, 16.0 * (double)nbat * (double)b_stride, st);
             TB_CUDA(launch_pass(d, pp, grid, st));
+        }
+
+        if (P.open_k) {  // Algorithm 2: join, late crossings, FP64 output
+            const int k = P.open_k;
+            float2* halves = boundary + (int64_t)batch * b_stride;
+            const int64_t h_stride = b_stride / 2;
+            JoinParams jp;
+            jp.B = boundary;
+            jp.b_stride = b_stride;
+            jp.tiles_per_b = b_stride / JOIN_TILE;
+            jp.ntiles = (int64_t)nbat * jp.tiles_per_b;
+            jp.E = tab<float2>(d_ws, L.open_E);
+            {
+                ProfScope ps(PC_JOIN, 16.0 * (double)nbat * (double)b_stride, st);
+                TB_CUDA(launch_join(k, jp, (int)std::min<int64_t>(jp.ntiles, 3LL * nsm), st));
+            }
+            const OpenOp* ops = tab<OpenOp>(d_ws, L.open_ops);
+            float2* cur = boundary;
+            int64_t cur_stride = b_stride;
+            for (int i = 0; i + 1 < (int)P.open_seg.size(); ++i) {
+                float2* nxt = (i % 2 == 0) ? halves : boundary;
+                const int64_t nxt_stride = (i % 2 == 0) ? h_stride : b_stride;
+                LateParams lp;
+                lp.in = cur;
+                lp.in_stride = cur_stride;
+                lp.out = nxt;
+                lp.out_stride = nxt_stride;
+                lp.out_entries = (int64_t)1 << (P.h - 1 - i);
+                lp.nbatch = nbat;
+                lp.k = k;
+                lp.ops = ops + P.open_seg[i];
+                lp.nops = P.open_seg[i + 1] - P.open_seg[i];
+                const int64_t chunks = ((lp.out_entries + (1 << OPEN_CHUNK_BITS) - 1) >> OPEN_CHUNK_BITS) * nbat;
+                ProfScope ps(PC_LATE, 24.0 * (double)nbat * (double)lp.out_entries, st);
+                TB_CUDA(launch_late(lp, (int)std::min<int64_t>(chunks, 8LL * nsm), st));
+                cur = nxt;
+                cur_stride = nxt_stride;
+            }
+            OpenFinalParams op;
+            op.Z = cur;
+            op.b_stride = cur_stride;
+            op.exps = exps;
+            op.sstride = sstride;
+            op.nslots = c.nslots;
+            op.k = k;
+            op.out = d_out + 2 * b0 * amps_per_row(P);
+            ProfScope ps(PC_FINAL, 0.0, st);
+            TB_CUDA(launch_open_finalize(op, nbat, st));
+            continue;
         }
 
         ReduceParams rp;
@@ -327,6 +380,55 @@ int tb_plan_create(int n, int d, const uint8_t* cliff, const uint8_t* tmask, con
     }
 }
 
+int tb_plan_create_open(int n, int d, const uint8_t* cliff, const uint8_t* tmask, const tb_gate1q* extra,
+                        int n_extra, const tb_opts* opts, int k, tb_plan** out) {
+    if (!out) return fail(TB_EINVAL, "out is NULL");
+    *out = nullptr;
+    const int h = (d + 1) / 2;
+    if (k < 1 || k > d / 4 || k > OPEN_MAX_K || k > n - 1)
+        return fail(TB_EDOMAIN, "open bits k must satisfy 1 <= k <= min(floor(d/4), 10, n-1)");
+    if (h <= SMALL_H_MAX) return fail(TB_EDOMAIN, "open plans need ceil(d/2) >= 13");
+    try {
+        tb_plan* p = new tb_plan;
+        p->p.open_k = k;
+        std::string err;
+        const int rc = plan_build(p->p, n, d, cliff, tmask, extra, n_extra, opts, err);
+        if (rc != TB_OK) {
+            delete p;
+            return fail(rc, err);
+        }
+        p->p.uid = next_plan_uid();
+        *out = p;
+        return TB_OK;
+    } catch (const std::bad_alloc&) {
+        return fail(TB_ENOMEM, "host allocation failed");
+    } catch (...) {
+        return fail(TB_EINVAL, "plan construction failed");
+    }
+}
+
+int tb_batched_sample(const double* amps, int k, int64_t na, const double* u, int32_t* b, double* q) {
+    if (!amps || !u || !b || k < 0 || k > 30 || na < 0) return fail(TB_EINVAL, "NULL or out-of-range argument");
+    const int64_t B = (int64_t)1 << k;
+    for (int64_t a = 0; a < na; ++a) {
+        const double* z = amps + 2 * a * B;
+        double Q = 0.0;
+        for (int64_t y = 0; y < B; ++y) Q += z[2 * y] * z[2 * y] + z[2 * y + 1] * z[2 * y + 1];
+        if (q) q[a] = Q;
+        if (!(u[a] >= 0.0 && u[a] < 1.0)) return fail(TB_EINVAL, "uniform variates must lie in [0, 1)");
+        // inverse of the conditional distribution function p(b | a) = p(a, b) / Q_a
+        const double target = u[a] * Q;
+        double acc = 0.0;
+        int64_t pick = B - 1;
+        for (int64_t y = 0; y < B; ++y) {
+            acc += z[2 * y] * z[2 * y] + z[2 * y + 1] * z[2 * y + 1];
+            if (acc > target) { pick = y; break; }
+        }
+        b[a] = (int32_t)pick;
+    }
+    return TB_OK;
+}
+
 int tb_plan_info(const tb_plan* plan, tb_plan_info_t* info) {
     if (!plan || !info) return fail(TB_EINVAL, "NULL argument");
     const Plan& P = plan->p;
@@ -340,6 +442,8 @@ int tb_plan_info(const tb_plan* plan, tb_plan_info_t* info) {
     info->n_steps = (int)P.steps.size();
     info->n_passes = P.n_pass_launches();
     info->table_bytes = P.lay.total;
+    info->open_k = P.open_k;
+    info->open_width = P.open_k ? std::max(P.h, 2 * P.open_k) : 0;
     return TB_OK;
 }
 
@@ -408,19 +512,19 @@ int tb_amplitudes(const tb_plan* plan, const uint8_t* bits, int64_t nb, void* d_
     const Plan& P = plan->p;
     if (P.h > MAX_H) return fail(TB_EDOMAIN, "boundary wider than 2^33 entries");
     if (nb == 0) return TB_OK;
-    for (int64_t i = 0; i < nb * P.n; ++i)
+    for (int64_t i = 0; i < nb * in_row(P); ++i)
         if (bits[i] > 1) return fail(TB_EINVAL, "bitstring entries must be 0 or 1");
     const int64_t stage = staging_bytes(P, nb);
     if (ws_bytes < P.lay.total + stage) return fail(TB_ENOMEM, "workspace too small for the staged inputs");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     uint8_t* ws = static_cast<uint8_t*>(d_ws);
     uint8_t* d_bits = ws + P.lay.total;
-    double* d_out = reinterpret_cast<double*>(ws + P.lay.total + align_up(nb * P.n, 256));
+    double* d_out = reinterpret_cast<double*>(ws + P.lay.total + align_up(nb * in_row(P), 256));
     TB_CUDA(cudaMemcpyAsync(d_ws, P.blob.data(), (size_t)P.lay.total, cudaMemcpyHostToDevice, st));
-    TB_CUDA(cudaMemcpyAsync(d_bits, bits, (size_t)(nb * P.n), cudaMemcpyHostToDevice, st));
+    TB_CUDA(cudaMemcpyAsync(d_bits, bits, (size_t)(nb * in_row(P)), cudaMemcpyHostToDevice, st));
     const int rc = run_device(P, d_bits, nb, d_ws, ws_bytes, P.lay.total + stage, d_out, st);
     if (rc != TB_OK) return rc;
-    TB_CUDA(cudaMemcpyAsync(out, d_out, (size_t)(16 * nb), cudaMemcpyDeviceToHost, st));
+    TB_CUDA(cudaMemcpyAsync(out, d_out, (size_t)(16 * nb * amps_per_row(P)), cudaMemcpyDeviceToHost, st));
     TB_CUDA(cudaStreamSynchronize(st));
     return TB_OK;
 }
@@ -468,6 +572,7 @@ int tb_amplitudes_noalloc(const tb_plan* plan, const uint8_t* d_bits, int64_t nb
     if (!plan || nb < 0 || (nb > 0 && (!d_bits || !d_out))) return fail(TB_EINVAL, "NULL or negative argument");
     const Plan& P = plan->p;
     if (P.h > MAX_H) return fail(TB_EDOMAIN, "boundary wider than 2^33 entries");
+    if (P.open_k) return fail(TB_EINVAL, "open plans are evaluated by tb_amplitudes / tb_amplitudes_device");
     const int64_t need = P.lay.total + call_layout(P).per_b;
     if (need > NOALLOC_SCRATCH_BYTES)
         return fail(TB_ENOMEM, "this circuit needs " + std::to_string(need) +

@@ -56,6 +56,10 @@ bool layout_of(const tb_batch_item* items, int nitems, Layout& L, std::string& e
             err = "item " + std::to_string(i) + ": boundary wider than 2^33 entries";
             return false;
         }
+        if (P.open_k) {
+            err = "item " + std::to_string(i) + ": open plans are evaluated by tb_amplitudes / tb_amplitudes_device";
+            return false;
+        }
         const CallLayout c = call_layout(P);
         const int64_t len = align_up(P.lay.total, 256) + it.nb * c.per_b;
         L.off.push_back(off);

@@ -1,0 +1,182 @@
+// Device kernels of an open plan (Algorithm 2): join of the early region with
+// the boundary, late-region crossings, and the final FP64 scaling.
+//
+// Boundary layout after the sweep of rows 0..n-k-1: entry (r << k) | s holds
+// B[sigma], s = the k crossing bits of the early region (address bits
+// 0..k-1), r = the late crossing bits (address bits k..h-1, the next one to
+// be contracted lowest).
+
+#include "open_kernels.cuh"
+
+namespace tb {
+
+namespace {
+
+__device__ __forceinline__ float2 cmac(float2 acc, float2 a, float2 b) {
+    acc.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x));
+    acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
+    return acc;
+}
+
+// Join: Z[r][y] = sum_s B[r][s] E[s][y], in place. A CTA owns JOIN_TILE
+// consecutive entries (R = JOIN_TILE / 2^k whole rows), copies them to shared
+// memory, then each thread computes a TR x TC register tile of outputs over
+// all s (E rows read through L1/L2, TC consecutive columns per thread) and
+// writes them back over the rows it read.
+template <int K>
+__global__ void __launch_bounds__(256) join_kernel(const JoinParams p) {
+    constexpr int NY = 1 << K;
+    constexpr int R = JOIN_TILE / NY;
+    constexpr int TC = NY < 8 ? NY : 8;
+    constexpr int NCG = NY / TC;       // column groups
+    constexpr int TR = 32 / TC;        // rows per thread
+    static_assert((256 / NCG) * TR == R, "join tiling");
+    extern __shared__ __align__(16) float2 sB[];
+    const int tid = threadIdx.x;
+    const int cg = tid % NCG, rg = tid / NCG;
+    const float2* __restrict__ E = p.E;
+    for (int64_t tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
+        const int64_t b = tile / p.tiles_per_b;
+        const int64_t t = tile - b * p.tiles_per_b;
+        float2* Z = p.B + b * p.b_stride + t * JOIN_TILE;
+        __syncthreads();  // previous tile's readers are done with sB
+        for (int i = tid; i < JOIN_TILE / 2; i += 256)
+            reinterpret_cast<float4*>(sB)[i] = reinterpret_cast<const float4*>(Z)[i];
+        __syncthreads();
+        float2 acc[TR][TC];
+#pragma unroll
+        for (int a = 0; a < TR; ++a)
+#pragma unroll
+            for (int c = 0; c < TC; ++c) acc[a][c] = make_float2(0.f, 0.f);
+        for (int s = 0; s < NY; ++s) {
+            float2 e[TC];
+#pragma unroll
+            for (int c = 0; c < TC; ++c) e[c] = __ldg(E + (int64_t)s * NY + cg * TC + c);
+#pragma unroll
+            for (int a = 0; a < TR; ++a) {
+                const float2 bv = sB[(rg * TR + a) * NY + s];
+#pragma unroll
+                for (int c = 0; c < TC; ++c) acc[a][c] = cmac(acc[a][c], bv, e[c]);
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < TR; ++a)
+#pragma unroll
+            for (int c = 0; c < TC; ++c) Z[(rg * TR + a) * NY + cg * TC + c] = acc[a][c];
+    }
+}
+
+// One late crossing: out[r'][y] = seg( in[2r'][y] + (-1)^(y_0) in[2r'+1][y] ).
+// A CTA works on chunks of 2^OPEN_CHUNK_BITS output entries (or one row when
+// 2^k is larger) in shared memory; the segment's operations act on chunk
+// index bits 0..k-1.
+__global__ void __launch_bounds__(256) late_kernel(const LateParams p) {
+    __shared__ float2 v[1 << OPEN_CHUNK_BITS];
+    __shared__ OpenOp ops[LATE_MAX_OPS];
+    const int tid = threadIdx.x;
+    for (int i = tid; i < p.nops; i += 256) ops[i] = p.ops[i];
+    const int NY = 1 << p.k;
+    const int chunk = NY > (1 << OPEN_CHUNK_BITS) ? NY : (1 << OPEN_CHUNK_BITS);  // k <= 10: 1024
+    const int64_t per_b = p.out_entries;  // output entries per batch element
+    const int64_t chunks_per_b = (per_b + chunk - 1) / chunk;
+    const int64_t nchunks = chunks_per_b * p.nbatch;
+    __syncthreads();
+    for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        const int64_t b = ch / chunks_per_b;
+        const int64_t o0 = (ch - b * chunks_per_b) * chunk;  // first output entry
+        const int len = (int)((per_b - o0) < chunk ? (per_b - o0) : chunk);
+        const float2* in = p.in + b * p.in_stride;
+        float2* out = p.out + b * p.out_stride;
+        __syncthreads();
+        for (int e = tid; e < len; e += 256) {
+            const int64_t o = o0 + e;
+            const int64_t rp = o >> p.k;
+            const int y = (int)(o & (NY - 1));
+            const float2 a = in[((2 * rp) << p.k) + y];
+            const float2 c = in[((2 * rp + 1) << p.k) + y];
+            v[e] = (y & 1) ? make_float2(a.x - c.x, a.y - c.y) : make_float2(a.x + c.x, a.y + c.y);
+        }
+        __syncthreads();
+        for (int q = 0; q < p.nops; ++q) {
+            const OpenOp& op = ops[q];
+            if (op.kind == 0) {
+                const int half = len >> 1;
+                for (int e = tid; e < half; e += 256) {
+                    const int lo = ((e >> op.j) << (op.j + 1)) | (e & ((1 << op.j) - 1));
+                    const int hi = lo | (1 << op.j);
+                    const float2 x0 = v[lo], x1 = v[hi];
+                    float2 r0 = make_float2(0.f, 0.f), r1 = make_float2(0.f, 0.f);
+                    r0 = cmac(cmac(r0, op.m[0], x0), op.m[1], x1);
+                    r1 = cmac(cmac(r1, op.m[2], x0), op.m[3], x1);
+                    v[lo] = r0;
+                    v[hi] = r1;
+                }
+            } else {
+                for (int e = tid; e < len; e += 256)
+                    if (((e >> op.j) & 1) && ((e >> (op.j + 1)) & 1)) v[e] = make_float2(-v[e].x, -v[e].y);
+            }
+            __syncthreads();
+        }
+        for (int e = tid; e < len; e += 256) out[o0 + e] = v[e];
+    }
+}
+
+// out[b][y] (FP64) = Z[b][y] * 2^(-sum of the sweep's rescaling exponents).
+__global__ void open_finalize_kernel(const OpenFinalParams p) {
+    const int64_t b = blockIdx.y;
+    double sc = 0.0;
+    for (int s = 0; s < p.nslots; ++s) sc += (double)p.exps[b * p.sstride + s];
+    const double f = exp2(-sc);
+    const int NY = 1 << p.k;
+    for (int y = blockIdx.x * blockDim.x + threadIdx.x; y < NY; y += gridDim.x * blockDim.x) {
+        const float2 z = p.Z[b * p.b_stride + y];
+        p.out[(b * NY + y) * 2] = (double)z.x * f;
+        p.out[(b * NY + y) * 2 + 1] = (double)z.y * f;
+    }
+}
+
+template <int K>
+cudaError_t launch_join_k(const JoinParams& p, int grid, cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute(join_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   JOIN_TILE * 8);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    join_kernel<K><<<grid, 256, JOIN_TILE * 8, st>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_join(int k, const JoinParams& p, int grid, cudaStream_t st) {
+    switch (k) {
+        case 1: return launch_join_k<1>(p, grid, st);
+        case 2: return launch_join_k<2>(p, grid, st);
+        case 3: return launch_join_k<3>(p, grid, st);
+        case 4: return launch_join_k<4>(p, grid, st);
+        case 5: return launch_join_k<5>(p, grid, st);
+        case 6: return launch_join_k<6>(p, grid, st);
+        case 7: return launch_join_k<7>(p, grid, st);
+        case 8: return launch_join_k<8>(p, grid, st);
+        case 9: return launch_join_k<9>(p, grid, st);
+        case 10: return launch_join_k<10>(p, grid, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_late(const LateParams& p, int grid, cudaStream_t st) {
+    if (p.nops > LATE_MAX_OPS || p.k > OPEN_CHUNK_BITS) return cudaErrorInvalidValue;
+    late_kernel<<<grid, 256, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_open_finalize(const OpenFinalParams& p, int nbatch, cudaStream_t st) {
+    const int NY = 1 << p.k;
+    dim3 grid((unsigned)((NY + 255) / 256), (unsigned)nbatch);
+    open_finalize_kernel<<<grid, 256, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace tb

@@ -1,0 +1,47 @@
+// Device kernels of an open plan (Algorithm 2): launch interface.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "tb_internal.h"
+
+namespace tb {
+
+constexpr int LATE_MAX_OPS = 128;  // operations of one late segment
+
+struct JoinParams {
+    float2* B;             // boundary of batch element 0 (joined in place)
+    int64_t b_stride;      // entries between batch elements
+    int64_t tiles_per_b;   // 2^h / JOIN_TILE
+    int64_t ntiles;        // nbatch * tiles_per_b
+    const float2* E;       // 2^k x 2^k early-region matrix
+};
+
+struct LateParams {
+    const float2* in;      // 2 * out_entries entries per batch element
+    int64_t in_stride;
+    float2* out;           // out_entries entries per batch element
+    int64_t out_stride;
+    int64_t out_entries;
+    int nbatch;
+    int k;
+    const OpenOp* ops;     // the segment after this crossing
+    int nops;
+};
+
+struct OpenFinalParams {
+    const float2* Z;       // 2^k entries per batch element
+    int64_t b_stride;
+    const int32_t* exps;   // rescaling exponents of the sweep
+    int64_t sstride;
+    int nslots;
+    int k;
+    double* out;           // (re, im) of 2^k amplitudes per batch element
+};
+
+cudaError_t launch_join(int k, const JoinParams& p, int grid, cudaStream_t st);
+cudaError_t launch_late(const LateParams& p, int grid, cudaStream_t st);
+cudaError_t launch_open_finalize(const OpenFinalParams& p, int nbatch, cudaStream_t st);
+
+}  // namespace tb

@@ -122,7 +122,7 @@ static bool build_passes(Plan& P, const std::vector<int>& sizes, std::vector<Pas
     // window of each step
     std::vector<Group> groups;
     int s = 0;
-    for (int r = 1; r <= P.n - 2; ++r) {
+    for (int r = 1; r <= P.last_mid_row(); ++r) {
         const bool fwd = (r % 2) == 1;
         for (int i = 0; i < h; ++i, ++s) {
             const int p = P.step_tgt[s];
@@ -317,7 +317,7 @@ int plan_build(Plan& P, int n, int d, const uint8_t* cliff, const uint8_t* tmask
     // ---- paired steps of rows 1..n-2
     P.steps.clear(); P.steps64.clear(); P.step_tgt.clear(); P.step_ctl.clear(); P.step_xq.clear();
     P.row_end.clear();
-    for (int r = 1; r <= n - 2; ++r) {
+    for (int r = 1; r <= P.last_mid_row(); ++r) {
         const bool fwd = (r % 2) == 1;
         for (int i = 0; i < h; ++i) {
             const int p = fwd ? i : h - 1 - i;
@@ -457,11 +457,11 @@ int plan_build(Plan& P, int n, int d, const uint8_t* cliff, const uint8_t* tmask
         return TB_EINVAL;
     }
     if (P.opts.precision != TB_PRECISION_FP32) {
-        if (h > SMALL_H_MAX && n > 2) {
+        if (h > SMALL_H_MAX && P.last_mid_row() >= 1) {
             const int rc = tc_schedule(P, err);
             if (rc != TB_OK) return rc;
         }
-    } else if (h > SMALL_H_MAX && n > 2) {
+    } else if (h > SMALL_H_MAX && P.last_mid_row() >= 1) {
         int mmax = P.opts.window_bits ? P.opts.window_bits : MAX_WINDOW;
         if (mmax < MIN_WINDOW || mmax > MAX_WINDOW) { err = "window_bits must be in 5..10"; return TB_EINVAL; }
         const int b_lo = P.opts.bottom_bits ? P.opts.bottom_bits : MIN_WINDOW;
@@ -490,6 +490,10 @@ int plan_build(Plan& P, int n, int d, const uint8_t* cliff, const uint8_t* tmask
     }
 
     sym_alg1(n, d, &P.width, &P.log2cost);
+    if (P.open_k > 0) {
+        const int rc = open_tables(P, err);
+        if (rc != TB_OK) return rc;
+    }
 
     // ---- device table image
     TableLayout& L = P.lay;
@@ -508,6 +512,9 @@ int plan_build(Plan& P, int n, int d, const uint8_t* cliff, const uint8_t* tmask
     L.red_mid = put((int64_t)P.red_mid.size() * 8);
     L.red_top = put((int64_t)P.red_top.size() * 8);
     L.tc_mats = put((int64_t)P.tc_mats.size());
+    L.open_E = put((int64_t)P.open_E.size() * 8);
+    L.open_ops = put((int64_t)P.open_ops.size() * (int64_t)sizeof(OpenOp));
+    L.open_seg = put((int64_t)P.open_seg.size() * 4);
     L.total = off;
     P.blob.assign((size_t)L.total, 0);
     auto cp = [&](int64_t o, const void* src, size_t bytes) {
@@ -525,6 +532,9 @@ int plan_build(Plan& P, int n, int d, const uint8_t* cliff, const uint8_t* tmask
     cp(L.red_mid, P.red_mid.data(), P.red_mid.size() * 8);
     cp(L.red_top, P.red_top.data(), P.red_top.size() * 8);
     cp(L.tc_mats, P.tc_mats.data(), P.tc_mats.size());
+    cp(L.open_E, P.open_E.data(), P.open_E.size() * 8);
+    cp(L.open_ops, P.open_ops.data(), P.open_ops.size() * sizeof(OpenOp));
+    cp(L.open_seg, P.open_seg.data(), P.open_seg.size() * 4);
     return TB_OK;
 }
 

@@ -374,6 +374,7 @@ int tb_server_submit(tb_server* S, const tb_plan* plan, const uint8_t* bits, int
     if (!S || !plan || !bits || !out || !ticket || nb <= 0) return fail(TB_EINVAL, "NULL argument or nb <= 0");
     const Plan& P = plan->p;
     if (P.h > MAX_H) return fail(TB_EDOMAIN, "boundary wider than 2^33 entries");
+    if (P.open_k) return fail(TB_EINVAL, "open plans are evaluated by tb_amplitudes / tb_amplitudes_device");
     for (int64_t i = 0; i < nb * P.n; ++i)
         if (bits[i] > 1) return fail(TB_EINVAL, "bitstring entries must be 0 or 1");
     const CallLayout c = call_layout(P);

@@ -113,6 +113,17 @@ __host__ __device__ constexpr int64_t tc_mat_bytes(int WB, int elem_bytes) {
     return 2LL * (2LL << WB) * (2LL << WB) * elem_bytes;
 }
 
+// ---- Open output bits (Algorithm 2): a batch of 2^k amplitudes per prefix --
+// One operation of the open band's late region (band qubit j = q - (n-k)).
+struct OpenOp {
+    int kind;     // 0: one-qubit gate m on band bit j; 1: CZ on band bits j, j+1
+    int j;
+    float2 m[4];  // row-major 2x2 (kind 0)
+};
+constexpr int OPEN_MAX_K = 10;          // 2^k x 2^k early-region matrix built on the host
+constexpr int OPEN_CHUNK_BITS = 10;     // late-region kernels work on 1024-entry chunks
+constexpr int JOIN_TILE = 8192;         // join kernel: boundary entries per CTA tile
+
 // Byte offsets of the device tables inside the workspace head.
 struct TableLayout {
     int64_t steps;     // StepG[n_steps]
@@ -127,6 +138,9 @@ struct TableLayout {
     int64_t red_mid;   // float2[2^m][4]       last row: 2x2 matrices
     int64_t red_top;   // float2[2][2^top][2]  last row: [x] row vectors
     int64_t tc_mats;   // split dense-block matrices of the tensor-core passes
+    int64_t open_E;    // float2[2^k][2^k]: early region joined with the first late ops
+    int64_t open_ops;  // OpenOp[]: late-region band operations
+    int64_t open_seg;  // int32[h-k+1]: ops of late crossing i are [seg[i], seg[i+1])
     int64_t total;
 };
 

@@ -36,6 +36,12 @@ struct Plan {
     std::vector<TcPass> tc_passes;
     std::vector<uint8_t> tc_mats;
     int tc_wb = 0;
+    // open output bits (Algorithm 2): the sweep stops after row n-k-1
+    int open_k = 0;
+    std::vector<float2> open_E;
+    std::vector<OpenOp> open_ops;
+    std::vector<int32_t> open_seg;
+    int last_mid_row() const { return open_k ? n - open_k - 1 : n - 2; }
     int n_pass_launches() const {
         return opts.precision != TB_PRECISION_FP32 ? (int)tc_passes.size() : (int)passes.size();
     }
@@ -51,6 +57,9 @@ struct Plan {
 };
 
 uint64_t next_plan_uid();
+
+// Early-region matrix and late-region operations of an open plan (open_plan.cpp).
+int open_tables(Plan& P, std::string& err);
 
 // Build the dense tensor-core schedule and its split matrices (tc_plan.cpp).
 int tc_schedule(Plan& P, std::string& err);

@@ -29,10 +29,14 @@ struct CallLayout {
     int red_blocks = 0;          // reduction blocks
     int64_t partial_bytes = 0;   // reduction partial sums
     int64_t boundary_bytes = 0;  // the boundary, 8 * 2^h
+    int64_t half_bytes = 0;      // open plans: second late-region buffer, 8 * 2^(h-1)
     int64_t per_b = 0;
 };
 
 bool small_path(const Plan& P);
+// Bytes of one input row (a bitstring, or an open plan's prefix) and amplitudes per row.
+inline int64_t in_row(const Plan& P) { return P.open_k ? P.n - P.open_k : P.n; }
+inline int64_t amps_per_row(const Plan& P) { return (int64_t)1 << P.open_k; }
 CallLayout call_layout(const Plan& P);
 int64_t max_batch(const Plan& P, const CallLayout& c);
 int num_sms();

@@ -152,7 +152,7 @@ int tc_schedule(Plan& P, std::string& err) {
     // ---- cut every row into chunks; merge the turn at address bit 0
     std::vector<Chunk> chunks;
     int s0 = 0;
-    for (int r = 1; r <= n - 2; ++r) {
+    for (int r = 1; r <= P.last_mid_row(); ++r) {
         const bool fwd = (r % 2) == 1;
         auto step_of_target = [&](int p) { return s0 + (fwd ? p : h - 1 - p); };
         if (fwd) {

@@ -1,6 +1,7 @@
 """Host-side checks of the C-ABI library: it loads, exports every declared
 symbol, and its planner reproduces the numbers the paper prints. No CUDA call
 is made (the planner is host-only), so these run without a GPU."""
+import ctypes
 import json
 import math
 import os
@@ -199,3 +200,68 @@ def test_dense_schedule_options(tb):
     base = tb.Plan(70, 64).info["table_bytes"]
     assert tb.Plan(70, 64, precision="bf16x3").info["table_bytes"] >= base + 375 * 2 * 128 * 128 * 2
     assert tb.Plan(70, 64, precision="tf32x3").info["table_bytes"] >= base + 443 * 2 * 64 * 64 * 4
+
+
+# ------------------------------------------------ open output bits (Algorithm 2)
+
+def test_open_plan_domain_and_width(tb):
+    """Algorithm 2 needs 1 <= k <= floor(d/4) (here also k <= 10, k <= n-1 and
+    width >= 13); its path keeps width ceil(d/2) (Proposition 2)."""
+    for n, d, k in [(16, 26, 6), (70, 64, 8), (70, 70, 10), (40, 66, 10), (13, 26, 1), (4, 26, 3)]:
+        p = tb.Plan(n, d, open_k=k)
+        assert p.info["open_k"] == k and p.info["open_width"] == (d + 1) // 2
+        assert p.row_bytes == n - k
+    for n, d, k in [(16, 26, 7), (12, 40, 12), (8, 24, 2), (70, 64, 11), (5, 40, 5)]:
+        with pytest.raises(tb.TbError) as e:
+            tb.Plan(n, d, open_k=k)
+        assert e.value.status == tb.TB_EDOMAIN
+    h = ctypes.c_void_p()
+    assert tb._lib.tb_plan_create_open(16, 26, None, None, None, 0, None, 0, ctypes.byref(h)) == tb.TB_EDOMAIN
+
+
+def test_open_plan_sweeps_only_the_fixed_region(tb):
+    """The sweep absorbs rows 1..n-k-1 as middle rows: (n-k-1) h paired steps."""
+    for n, d, k in [(16, 26, 3), (30, 40, 8), (70, 64, 8)]:
+        assert tb.Plan(n, d, open_k=k).info["n_steps"] == (n - k - 1) * (d // 2)
+    # the workspace holds one boundary and half a boundary per prefix
+    p = tb.Plan(30, 40, open_k=8)
+    assert p.workspace_min_bytes() >= p.info["table_bytes"] + 12 * 2 ** 20
+
+
+def test_batched_sample_inverts_the_conditional_distribution(tb):
+    """Sec. 4 batched sampler: b is the smallest suffix whose cumulative
+    probability exceeds u Q_a; Q_a is the prefix's marginal mass."""
+    rng = np.random.default_rng(1)
+    for k in (1, 3, 8):
+        amps = rng.standard_normal((5, 1 << k)) + 1j * rng.standard_normal((5, 1 << k))
+        u = rng.random(5)
+        b, q = tb.batched_sample(amps, u)
+        p = np.abs(amps) ** 2
+        np.testing.assert_allclose(q, p.sum(axis=1), rtol=1e-14)
+        cdf = np.cumsum(p, axis=1)
+        ref = np.array([np.searchsorted(cdf[a], u[a] * cdf[a, -1], side="right") for a in range(5)])
+        np.testing.assert_array_equal(b, np.minimum(ref, (1 << k) - 1))
+    # boundary variates: u = 0 picks the first suffix with mass, u -> 1 the last
+    z = np.array([[0, 0, 1, 1, 0, 0, 0, 0]], np.complex128)
+    assert tb.batched_sample(z, [0.0])[0][0] == 2
+    assert tb.batched_sample(z, [0.999999])[0][0] == 3
+    with pytest.raises(tb.TbError):
+        tb.batched_sample(z, [1.0])
+
+
+def test_batched_sampling_tv_identity(oracle_mod):
+    """Sec. 4: with prefixes drawn uniformly, the batched sampler's output
+    distribution q_k(a, b) = p(a, b) / (A Q_a) is at total variation
+    distance (1/2) sum_a |Q_a - 1/A| from p. Checked exactly on the FP64 state
+    vector of a small circuit (it pins the identity, not the sampler code)."""
+    c = W.random_circuit(10, 12, 10, 0, 77)
+    psi = oracle_mod.sv_state(c.n, c.d, oracle_mod.circuit_gates(c))
+    p = np.abs(psi) ** 2
+    k = 3
+    A = 1 << (c.n - k)
+    # state index = sum_q x_q 2^q: prefix qubits 0..n-k-1 are the low bits
+    pk = p.reshape(1 << k, A)  # [b, a]
+    Q = pk.sum(axis=0)
+    q = pk / (A * Q[None, :])
+    tv = 0.5 * np.abs(q - pk).sum()
+    assert abs(tv - 0.5 * np.abs(Q - 1.0 / A).sum()) < 1e-12

@@ -1,0 +1,122 @@
+"""Open output bits (Algorithm 2): one evaluation returns the 2^k amplitudes
+<a, b|U|0^n> of a prefix a, compared with the plain definition (FP64 state
+vector or naive boundary) element by element."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def tb():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2608_13110_gb300 import build as b
+    b.build()
+    import paper_2608_13110_gb300 as mod
+    return mod
+
+
+def full_bits(prefixes, n, k):
+    """Every (a, b) bitstring, row-major over (prefix, y), b_j = bit j of y."""
+    na = prefixes.shape[0]
+    out = np.zeros((na, 1 << k, n), np.uint8)
+    out[:, :, : n - k] = prefixes[:, None, :]
+    y = np.arange(1 << k)
+    for j in range(k):
+        out[:, :, n - k + j] = (y >> j) & 1
+    return out.reshape(-1, n)
+
+
+def rel_l2(a, ref):
+    return float(np.linalg.norm(a - ref) / np.linalg.norm(ref))
+
+
+@pytest.mark.parametrize("n,d,k", [(16, 26, 3), (16, 26, 6), (13, 26, 1), (15, 28, 5), (14, 30, 7),
+                                   (17, 26, 2), (5, 26, 4), (4, 26, 3)])
+def test_state_vector(tb, oracle_mod, n, d, k):
+    """Widths 13..15, both parities of the crossing layers (n-k-1 even and
+    odd), k = 1..7, and fixed regions of a single row (n - k = 1)."""
+    c = W.random_circuit(n, d, None, 0, 1300 + 10 * n + k)
+    rng = np.random.default_rng(n * 100 + k)
+    prefixes = rng.integers(0, 2, size=(3, n - k), dtype=np.uint8)
+    plan = tb.Plan.from_circuit(c, open_k=k)
+    assert plan.info["open_width"] == (d + 1) // 2  # Proposition 2: width ceil(d/2)
+    got = plan.amplitudes(prefixes)
+    assert got.shape == (3, 1 << k)
+    ref = oracle_mod.sv_amplitudes(n, d, oracle_mod.circuit_gates(c), full_bits(prefixes, n, k)).reshape(3, -1)
+    for i in range(3):
+        assert rel_l2(got[i], ref[i]) < TOL
+
+
+def test_naive_boundary_sampled_30_40(tb, oracle_mod):
+    """n = 30, d = 40 (width 20), k = 8: 256 amplitudes per prefix; eight
+    sampled suffixes per prefix against the FP64 naive boundary."""
+    c = W.slice_30_40(nb=0)
+    k = 8
+    rng = np.random.default_rng(5)
+    prefixes = rng.integers(0, 2, size=(2, c.n - k), dtype=np.uint8)
+    got = tb.Plan.from_circuit(c, open_k=k).amplitudes(prefixes)
+    ys = rng.choice(1 << k, size=8, replace=False)
+    bits = full_bits(prefixes, c.n, k).reshape(2, 1 << k, c.n)[:, ys, :].reshape(-1, c.n)
+    ref = oracle_mod.nb_amplitudes(c.n, c.d, oracle_mod.circuit_gates(c), bits).reshape(2, -1)
+    assert rel_l2(got[:, ys].reshape(-1), ref.reshape(-1)) < TOL
+
+
+def test_matches_the_plain_sweep_at_70_56(tb):
+    """n = 70, d = 56 (width 28), k = 8: the open plan's batch equals the
+    single-amplitude sweep on the same bitstrings."""
+    c = W.scale_70_56(nb=0)
+    k = 8
+    prefix = np.random.default_rng(9).integers(0, 2, size=(1, c.n - k), dtype=np.uint8)
+    got = tb.Plan.from_circuit(c, open_k=k).amplitudes(prefix)[0]
+    ys = np.array([0, 1, 37, 128, 255])
+    bits = full_bits(prefix, c.n, k)[ys]
+    ref = tb.Plan.from_circuit(c).amplitudes(bits)
+    assert rel_l2(got[ys], ref) < TOL
+    # the batch is a conditional distribution's support: Q_a > 0
+    assert np.sum(np.abs(got) ** 2) > 0
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+def test_split_precision_sweep(tb, oracle_mod, prec):
+    c = W.random_circuit(16, 28, None, 0, 1400)
+    k = 4
+    prefixes = np.random.default_rng(3).integers(0, 2, size=(2, 12), dtype=np.uint8)
+    got = tb.Plan.from_circuit(c, open_k=k, precision=prec).amplitudes(prefixes)
+    ref = oracle_mod.sv_amplitudes(16, 28, oracle_mod.circuit_gates(c), full_bits(prefixes, 16, k)).reshape(2, -1)
+    assert rel_l2(got.reshape(-1), ref.reshape(-1)) < (2e-5 if prec == "tf32x3" else 1.5e-4)
+
+
+def test_device_entry_and_batch_split(tb):
+    """Device-resident prefixes; a workspace for one prefix evaluates many in
+    turn with the same result."""
+    import torch
+    c = W.random_circuit(20, 30, None, 0, 1500)
+    k = 5
+    plan = tb.Plan.from_circuit(c, open_k=k)
+    prefixes = np.random.default_rng(4).integers(0, 2, size=(5, 15), dtype=np.uint8)
+    ws = torch.empty(plan.workspace_min_bytes(), dtype=torch.uint8, device="cuda")
+    plan.upload(ws)
+    d_out = torch.empty((5 << k, 2), dtype=torch.float64, device="cuda")
+    plan.amplitudes_device(torch.from_numpy(prefixes).cuda(), ws, d_out)
+    torch.cuda.synchronize()
+    dev = d_out.cpu().numpy().view(np.complex128).reshape(5, -1)
+    np.testing.assert_array_equal(dev, plan.amplitudes(prefixes))
+
+
+def test_open_plans_are_rejected_elsewhere(tb):
+    import torch
+    c = W.random_circuit(16, 26, None, 0, 1600)
+    plan = tb.Plan.from_circuit(c, open_k=3)
+    with pytest.raises(tb.TbError) as e:
+        plan.amplitudes_noalloc(torch.zeros((1, 13), dtype=torch.uint8, device="cuda"),
+                                torch.empty((8, 2), dtype=torch.float64, device="cuda"))
+    assert e.value.status == tb.TB_EINVAL
+    with pytest.raises(tb.TbError):
+        plan.amplitudes(np.full((1, 13), 2, np.uint8))
