@@ -457,6 +457,94 @@ def run_precision_workload(args, rank, world, local):
         print(json.dumps(line))
 
 
+def run_open_workload(args, rank, world, local):
+    """Algorithm 2 on the n=70, d=64 workload: k = 8 open output bits, so one
+    sweep of the fixed region (rows 0..61) plus the join and the late region
+    returns the 256 amplitudes of a prefix. value = amplitudes/s over
+    ``--nb-open`` uniform prefixes per step; compared with the plain sweep
+    (one amplitude per sweep) timed in the same run."""
+    import torch
+    import paper_2608_13110_gb300 as tb
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    k = 8
+    na = args.nb_open
+    c = W.precision_70_64(replica=rank, nb=1)
+    rng = np.random.default_rng(7000 + rank)
+    prefixes = rng.integers(0, 2, size=(na, c.n - k), dtype=np.uint8)
+    plan = tb.Plan.from_circuit(c, open_k=k, precision=args.precision)
+    info = plan.info
+    stream = torch.cuda.current_stream(dev)
+    ws = torch.empty(plan.workspace_bytes(na), dtype=torch.uint8, device=dev)
+    plan.upload(ws, stream)
+    d_pre = torch.from_numpy(prefixes).to(dev)
+    d_out = torch.empty((na << k, 2), dtype=torch.float64, device=dev)
+    for _ in range(args.warmup):
+        plan.amplitudes_device(d_pre, ws, d_out, stream)
+    torch.cuda.synchronize(dev)
+    barrier(world, dev)
+    clocks = ClockSampler(local)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    tb.profile_begin()
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.amplitudes_device(d_pre, ws, d_out, stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    prof = tb.profile_end()
+    clk = clocks.stop()
+    t = max_over_ranks(e0.elapsed_time(e1) / 1e3, world, dev)
+    amps = d_out.cpu().numpy().view(np.complex128).reshape(na, -1)
+    # end to end: host prefixes in, host amplitudes out
+    pre_pin = torch.from_numpy(prefixes).pin_memory()
+    out_pin = torch.empty((na << k, 2), dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    plan.amplitudes(pre_pin.numpy(), ws=ws, stream=stream, out=out_pin.numpy())
+    t_e2e = max_over_ranks(time.perf_counter() - t0, world, dev)
+    # the plain sweep on four of the same bitstrings, for the comparison and a cross-check
+    ys = np.array([0, 77, 200, 255])
+    bits = np.zeros((4, c.n), np.uint8)
+    bits[:, : c.n - k] = prefixes[0]
+    for j in range(k):
+        bits[:, c.n - k + j] = (ys >> j) & 1
+    pplan = tb.Plan.from_circuit(c, precision=args.precision)
+    pws = torch.empty(pplan.workspace_bytes(4), dtype=torch.uint8, device=dev)
+    pplan.upload(pws, stream)
+    d_bits = torch.from_numpy(bits).to(dev)
+    p_out = torch.empty((4, 2), dtype=torch.float64, device=dev)
+    pplan.amplitudes_device(d_bits, pws, p_out, stream)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    pplan.amplitudes_device(d_bits, pws, p_out, stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    t_plain = max_over_ranks(e0.elapsed_time(e1) / 1e3, world, dev)
+    plain_amps = p_out.cpu().numpy().view(np.complex128).reshape(-1)
+    agree = float(np.linalg.norm(amps[0, ys] - plain_amps) / np.linalg.norm(plain_amps))
+    b, q = tb.batched_sample(amps, rng.random(na))
+    total = max(1e-9, sum(v["ms"] for v in prof.values()))
+    line = {"metric": "amplitudes/s (n=70, d=64, k=8 open output bits: 256 amplitudes per sweep)",
+            "value": world * na * (1 << k) * args.steps / t, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "complex64", "data": "synthetic",
+            "config": {"workload": f"brickwork CZ n=70 d=64, random Cliffords, 426 T, k=8, {na} uniform prefixes/step",
+                       "open_k": k, "open_width": info["open_width"], "passes_per_prefix": info["n_passes"],
+                       "pass_arithmetic": args.precision, "parallelism": f"replicas x{world}"},
+            "e2e": {"value": world * na * (1 << k) / t_e2e, "unit": UNIT,
+                    "h2d_bytes_per_step": int(prefixes.nbytes + info["table_bytes"]),
+                    "d2h_bytes_per_step": int(16 * (na << k))},
+            "gpu_launches": sum(v["launches"] for v in prof.values()),
+            "time_share": {c_: round(v["ms"] / total, 4) for c_, v in prof.items() if v["launches"]},
+            "plain": {"value": world * 4 / t_plain, "unit": UNIT, "how": "single-amplitude sweep, same circuit"},
+            "rel_l2_vs_plain_sweep": agree,
+            "sampled": {"suffixes": b.tolist()[:8], "Q_a_times_A": (q * 2.0 ** (c.n - k)).tolist()[:8]},
+            "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def run_serve_workload(args, rank, world, local):
     """Poisson stream (mean 20 requests/s) of amplitude requests, n ~ U[16,70],
     d even ~ U{8..44} (width <= 22), 1..256 bitstrings each,
@@ -537,10 +625,12 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="n70d64", choices=("n70d64", "batch", "serve", "precision"),
+    ap.add_argument("--workload", default="n70d64", choices=("n70d64", "batch", "serve", "precision", "open"),
                     help="n70d64: the headline metric; batch: 64 uneven circuits in one graph; "
                          "serve: Poisson request stream through the serving runtime; "
-                         "precision: FP32 vs 3xTF32 / 3xBF16 tensor-core passes with errors vs FP64")
+                         "precision: FP32 vs 3xTF32 / 3xBF16 tensor-core passes with errors vs FP64; "
+                         "open: Algorithm 2, 256 amplitudes per sweep (k=8)")
+    ap.add_argument("--nb-open", type=int, default=2, help="prefixes per step in the open workload")
     ap.add_argument("--precision", default="fp32", choices=("fp32", "tf32x3", "bf16x3"),
                     help="pass arithmetic of the n70d64 workload")
     ap.add_argument("--nb-precision", type=int, default=4, help="bitstrings per step in the precision workload")
@@ -558,6 +648,8 @@ def main():
             run_serve_workload(args, rank, world, local)
         elif args.workload == "precision":
             run_precision_workload(args, rank, world, local)
+        elif args.workload == "open":
+            run_open_workload(args, rank, world, local)
         else:
             run_ours(args, rank, world, local)
     if _env_int("WORLD_SIZE", 1) > 1:
