@@ -262,7 +262,7 @@ int run_device(const Plan& P, const uint8_t* d_bits, int64_t nb, void* d_ws, int
             jp.E = tab<float2>(d_ws, L.open_E);
             {
                 ProfScope ps(PC_JOIN, 16.0 * (double)nbat * (double)b_stride, st);
-                TB_CUDA(launch_join(k, jp, (int)std::min<int64_t>(jp.ntiles, 3LL * nsm), st));
+                TB_CUDA(launch_join(k, jp, (int)std::min<int64_t>(jp.ntiles, 2LL * nsm), st));
             }
             const OpenOp* ops = tab<OpenOp>(d_ws, L.open_ops);
             float2* cur = boundary;

@@ -19,44 +19,54 @@ __device__ __forceinline__ float2 cmac(float2 acc, float2 a, float2 b) {
 }
 
 // Join: Z[r][y] = sum_s B[r][s] E[s][y], in place. A CTA owns JOIN_TILE
-// consecutive entries (R = JOIN_TILE / 2^k whole rows), copies them to shared
-// memory, then each thread computes a TR x TC register tile of outputs over
-// all s (E rows read through L1/L2, TC consecutive columns per thread) and
-// writes them back over the rows it read.
+// consecutive entries (R = JOIN_TILE / 2^k whole rows) and copies them to
+// shared memory; E is staged through shared memory in chunks of SC rows
+// (32 KB) and used by every row of the tile. Each thread accumulates a TR x TC
+// register tile (TC consecutive columns, TR rows) over all s and finally
+// writes it back over the rows the CTA read.
 template <int K>
-__global__ void __launch_bounds__(256) join_kernel(const JoinParams p) {
+__global__ void __launch_bounds__(256, 2) join_kernel(const JoinParams p) {
     constexpr int NY = 1 << K;
     constexpr int R = JOIN_TILE / NY;
     constexpr int TC = NY < 8 ? NY : 8;
     constexpr int NCG = NY / TC;       // column groups
     constexpr int TR = 32 / TC;        // rows per thread
+    constexpr int SC = NY >= 64 ? 4096 / NY : NY;  // E rows per chunk (32 KB)
     static_assert((256 / NCG) * TR == R, "join tiling");
-    extern __shared__ __align__(16) float2 sB[];
+    static_assert(NY % SC == 0, "E chunks");
+    extern __shared__ __align__(16) float2 smem[];
+    float2* sB = smem;                 // JOIN_TILE entries
+    float2* sE = smem + JOIN_TILE;     // SC x NY entries
     const int tid = threadIdx.x;
     const int cg = tid % NCG, rg = tid / NCG;
-    const float2* __restrict__ E = p.E;
     for (int64_t tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
         const int64_t b = tile / p.tiles_per_b;
         const int64_t t = tile - b * p.tiles_per_b;
         float2* Z = p.B + b * p.b_stride + t * JOIN_TILE;
-        __syncthreads();  // previous tile's readers are done with sB
+        __syncthreads();  // the previous tile is done with sB and sE
         for (int i = tid; i < JOIN_TILE / 2; i += 256)
             reinterpret_cast<float4*>(sB)[i] = reinterpret_cast<const float4*>(Z)[i];
-        __syncthreads();
         float2 acc[TR][TC];
 #pragma unroll
         for (int a = 0; a < TR; ++a)
 #pragma unroll
             for (int c = 0; c < TC; ++c) acc[a][c] = make_float2(0.f, 0.f);
-        for (int s = 0; s < NY; ++s) {
-            float2 e[TC];
+        for (int s0 = 0; s0 < NY; s0 += SC) {
+            __syncthreads();  // sE free (and sB loaded on the first chunk)
+            for (int i = tid; i < SC * NY / 2; i += 256)
+                reinterpret_cast<float4*>(sE)[i] = __ldg(reinterpret_cast<const float4*>(p.E + (int64_t)s0 * NY) + i);
+            __syncthreads();
+#pragma unroll 4
+            for (int ss = 0; ss < SC; ++ss) {
+                float2 e[TC];
 #pragma unroll
-            for (int c = 0; c < TC; ++c) e[c] = __ldg(E + (int64_t)s * NY + cg * TC + c);
+                for (int c = 0; c < TC; ++c) e[c] = sE[ss * NY + cg * TC + c];
 #pragma unroll
-            for (int a = 0; a < TR; ++a) {
-                const float2 bv = sB[(rg * TR + a) * NY + s];
+                for (int a = 0; a < TR; ++a) {
+                    const float2 bv = sB[(rg * TR + a) * NY + s0 + ss];
 #pragma unroll
-                for (int c = 0; c < TC; ++c) acc[a][c] = cmac(acc[a][c], bv, e[c]);
+                    for (int c = 0; c < TC; ++c) acc[a][c] = cmac(acc[a][c], bv, e[c]);
+                }
             }
         }
 #pragma unroll
@@ -135,16 +145,18 @@ __global__ void open_finalize_kernel(const OpenFinalParams p) {
     }
 }
 
+constexpr int JOIN_SMEM = JOIN_TILE * 8 + 32 * 1024;  // boundary rows + one E chunk
+
 template <int K>
 cudaError_t launch_join_k(const JoinParams& p, int grid, cudaStream_t st) {
     static bool attr = false;
     if (!attr) {
         const cudaError_t e = cudaFuncSetAttribute(join_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   JOIN_TILE * 8);
+                                                   JOIN_SMEM);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    join_kernel<K><<<grid, 256, JOIN_TILE * 8, st>>>(p);
+    join_kernel<K><<<grid, 256, JOIN_SMEM, st>>>(p);
     return cudaGetLastError();
 }
 
