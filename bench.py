@@ -126,6 +126,18 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ CPU baseline
+def _cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name"):
+                return line.split(":", 1)[1].strip() + f" ({os.cpu_count()} logical CPUs)"
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return f"{platform.machine()} ({os.cpu_count()} logical CPUs)"
+
+
 def cpu_baseline(seconds_cap: float = 30.0) -> dict:
     """FP64 oracle (naive row-by-row contraction) on the n=30, d=40 slice with
     the workload's gate statistics, scaled to the n=70, d=64 workload by the
@@ -145,6 +157,7 @@ def cpu_baseline(seconds_cap: float = 30.0) -> dict:
     slice_rate = done / dt
     ratio = 2.0 ** (tb.Plan(70, 64).info["log2_cost"] - tb.Plan(*CPU_SAMPLE).info["log2_cost"])
     return {"value": slice_rate / ratio, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "cpu": _cpu_model(),
             "sample": (f"{done} amplitude(s) of an n={CPU_SAMPLE[0]}, d={CPU_SAMPLE[1]} slice (width 20) "
                        f"in {dt:.1f} s = {slice_rate:.3g} amps/s, divided by the Algorithm 1 cost ratio "
                        f"C(70,64)/C(30,40) = {ratio:.4g}")}
@@ -280,8 +293,13 @@ def run_ours(args, rank, world, local):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(c.bits.nbytes + info["table_bytes"]),
                 "d2h_bytes_per_step": int(16 * nb)},
         "gpu_launches": n_launch,
+        "unfused_equivalent_gbs": {
+            "value": world * nb * args.steps * info["n_steps"] * 16.0 * 2.0 ** h / t_dev_max / 1e9,
+            "how": "paired steps x 16 B x 2^h per amplitude / time: the bandwidth one HBM pass per step "
+                   "would need for the same amps/s (secondary, not a measured bandwidth)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": (achieved / hbm_peak) if achieved else None, "traffic": traffic,
+                     "traffic_over_algorithmic": (traffic / (16.0 * 2.0 ** h)) if traffic else None,
                      "kernel": "pass_kernel" if args.precision == "fp32" else "tc_pass_kernel",
                      "peak_source": f"{peak_src} copy bandwidth",
                      "pass_launches": p["launches"], "pass_ms_total": p["ms"],
