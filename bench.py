@@ -487,7 +487,11 @@ def run_open_workload(args, rank, world, local):
     torch.cuda.set_device(dev)
     k = 8
     na = args.nb_open
-    c = W.precision_70_64(replica=rank, nb=1)
+    if args.shape:  # profiling aid: a smaller circuit with the same statistics
+        n_, d_ = (int(v) for v in args.shape.split(","))
+        c = W.random_circuit(n_, d_, None, 1, 4000 + 100 * rank + d_)
+    else:
+        c = W.precision_70_64(replica=rank, nb=1)
     rng = np.random.default_rng(7000 + rank)
     prefixes = rng.integers(0, 2, size=(na, c.n - k), dtype=np.uint8)
     plan = tb.Plan.from_circuit(c, open_k=k, precision=args.precision)
@@ -543,11 +547,12 @@ def run_open_workload(args, rank, world, local):
     agree = float(np.linalg.norm(amps[0, ys] - plain_amps) / np.linalg.norm(plain_amps))
     b, q = tb.batched_sample(amps, rng.random(na))
     total = max(1e-9, sum(v["ms"] for v in prof.values()))
-    line = {"metric": "amplitudes/s (n=70, d=64, k=8 open output bits: 256 amplitudes per sweep)",
+    shape = f"n={c.n}, d={c.d}" + (" (--shape, profiling)" if args.shape else "")
+    line = {"metric": f"amplitudes/s ({shape}, k=8 open output bits: 256 amplitudes per sweep)",
             "value": world * na * (1 << k) * args.steps / t, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "complex64", "data": "synthetic",
-            "config": {"workload": f"brickwork CZ n=70 d=64, random Cliffords, 426 T, k=8, {na} uniform prefixes/step",
+            "config": {"workload": f"brickwork CZ {shape}, random Cliffords, {c.n_t} T, k=8, {na} uniform prefixes/step",
                        "open_k": k, "open_width": info["open_width"], "passes_per_prefix": info["n_passes"],
                        "pass_arithmetic": args.precision, "parallelism": f"replicas x{world}"},
             "e2e": {"value": world * na * (1 << k) / t_e2e, "unit": UNIT,

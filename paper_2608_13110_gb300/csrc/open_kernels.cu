@@ -22,8 +22,9 @@ __device__ __forceinline__ float2 cmac(float2 acc, float2 a, float2 b) {
 // consecutive entries (R = JOIN_TILE / 2^k whole rows) and copies them to
 // shared memory; E is staged through shared memory in chunks of SC rows
 // (32 KB) and used by every row of the tile. Each thread accumulates a TR x TC
-// register tile (TC consecutive columns, TR rows) over all s and finally
-// writes it back over the rows the CTA read.
+// register tile (columns cg, cg + NCG, ..., so that consecutive lanes read
+// consecutive E entries and write consecutive outputs; TR rows) over all s
+// and finally writes it back over the rows the CTA read.
 template <int K>
 __global__ void __launch_bounds__(256, 2) join_kernel(const JoinParams p) {
     constexpr int NY = 1 << K;
@@ -60,7 +61,7 @@ __global__ void __launch_bounds__(256, 2) join_kernel(const JoinParams p) {
             for (int ss = 0; ss < SC; ++ss) {
                 float2 e[TC];
 #pragma unroll
-                for (int c = 0; c < TC; ++c) e[c] = sE[ss * NY + cg * TC + c];
+                for (int c = 0; c < TC; ++c) e[c] = sE[ss * NY + cg + NCG * c];
 #pragma unroll
                 for (int a = 0; a < TR; ++a) {
                     const float2 bv = sB[(rg * TR + a) * NY + s0 + ss];
@@ -72,7 +73,7 @@ __global__ void __launch_bounds__(256, 2) join_kernel(const JoinParams p) {
 #pragma unroll
         for (int a = 0; a < TR; ++a)
 #pragma unroll
-            for (int c = 0; c < TC; ++c) Z[(rg * TR + a) * NY + cg * TC + c] = acc[a][c];
+            for (int c = 0; c < TC; ++c) Z[(rg * TR + a) * NY + cg + NCG * c] = acc[a][c];
     }
 }
 
