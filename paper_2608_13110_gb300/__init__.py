@@ -169,6 +169,27 @@ def batched_sample(amps, u):
     return b, q
 
 
+def sample(plan, n_samples: int, rng, ws=None):
+    """Batched sampling (Sec. 4) with an open plan (``open_k = k``): draw
+    n_samples prefixes a uniformly from {0,1}^(n-k), evaluate the 2^k
+    amplitudes of each on the device (one sweep per prefix), and draw one
+    suffix b per prefix from p(b | a) = |<a,b|U|0^n>|^2 / Q_a. ``rng`` is a
+    numpy Generator (the prefixes and the uniform variates come from it).
+    Returns (bitstrings (n_samples, n) uint8 with x_q = bits[:, q],
+    their amplitudes (n_samples,), Q_a (n_samples,))."""
+    k = plan.open_k
+    if k <= 0:
+        raise ValueError("batched sampling needs an open plan (open_k > 0)")
+    prefixes = rng.integers(0, 2, size=(int(n_samples), plan.n - k), dtype=np.uint8)
+    amps = plan.amplitudes(prefixes, ws=ws)
+    b, q = batched_sample(amps, rng.random(int(n_samples)))
+    bits = np.zeros((int(n_samples), plan.n), np.uint8)
+    bits[:, : plan.n - k] = prefixes
+    for j in range(k):
+        bits[:, plan.n - k + j] = (b >> j) & 1
+    return bits, amps[np.arange(int(n_samples)), b], q
+
+
 def device_faults() -> int:
     """Bounded device waits that gave up since the last call (and clear)."""
     c = ctypes.c_int32()

@@ -120,3 +120,40 @@ def test_open_plans_are_rejected_elsewhere(tb):
     assert e.value.status == tb.TB_EINVAL
     with pytest.raises(tb.TbError):
         plan.amplitudes(np.full((1, 13), 2, np.uint8))
+
+
+def test_maximum_width_33_every_suffix(tb, oracle_mod):
+    """n = 70, d = 66 (width 33: a 64 GiB boundary and a 32 GiB late-region
+    buffer), k = 8: all 256 amplitudes of a prefix against the closed form of
+    an H / diagonal / H circuit."""
+    from test_gpu_parity import _nonzero_bits
+    c = W.hdiag_circuit(70, 66, 439, 0, 4300)
+    k = 8
+    prefix = _nonzero_bits(c, oracle_mod, 1, 5)[:, : c.n - k]
+    got = tb.Plan.from_circuit(c, open_k=k).amplitudes(prefix)[0]
+    ref = oracle_mod.closed_form_hdiag(c, full_bits(prefix, c.n, k))
+    assert rel_l2(got, ref) < TOL
+
+
+def test_batched_sampling_draws_from_the_conditional(tb, oracle_mod):
+    """Sec. 4 sampler end to end: for every draw, the prefix is the caller's
+    uniform draw and the suffix is the inverse of p(. | a) (from the FP64 state
+    vector) at the caller's uniform variate."""
+    n, d, k = 14, 26, 4
+    c = W.random_circuit(n, d, None, 0, 1700)
+    plan = tb.Plan.from_circuit(c, open_k=k)
+    bits, amps, q = tb.sample(plan, 12, np.random.default_rng(11))
+    rng = np.random.default_rng(11)  # replay the same variates
+    prefixes = rng.integers(0, 2, size=(12, n - k), dtype=np.uint8)
+    u = rng.random(12)
+    np.testing.assert_array_equal(bits[:, : n - k], prefixes)
+    psi = oracle_mod.sv_state(n, d, oracle_mod.circuit_gates(c))
+    idx = oracle_mod.basis_index(full_bits(prefixes, n, k)).reshape(12, -1)
+    p = np.abs(psi[idx]) ** 2
+    np.testing.assert_allclose(q, p.sum(axis=1), rtol=1e-4)
+    cdf = np.cumsum(p, axis=1) / p.sum(axis=1, keepdims=True)
+    for i in range(12):
+        b = int(oracle_mod.basis_index(bits[i:i + 1, n - k:])[0])
+        lo = cdf[i, b - 1] if b > 0 else 0.0
+        assert lo - 1e-4 <= u[i] <= cdf[i, b] + 1e-4
+        assert abs(amps[i] - psi[oracle_mod.basis_index(bits[i:i + 1])[0]]) < 1e-5 * np.abs(psi).max() + 1e-6

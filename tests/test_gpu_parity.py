@@ -209,3 +209,15 @@ def test_edge_cases(tb, oracle_mod):
         c = W.random_circuit(2, d, None, 4, 90 + d)
         ref = oracle_mod.sv_amplitudes(2, d, oracle_mod.circuit_gates(c), all_bits(2))
         assert rel_l2(tb.Plan.from_circuit(c).amplitudes(all_bits(2)), ref) < TOL
+
+
+def test_maximum_width_33_closed_form(tb, oracle_mod):
+    """The widest boundary the device path evaluates: n = 70, d = 66, width 33
+    (2^33 complex64 = 64 GiB), against the exact amplitude of an H / diagonal /
+    H circuit (d = 2 mod 4: a chain sum)."""
+    c = W.hdiag_circuit(70, 66, 439, 0, 4300)
+    bits = _nonzero_bits(c, oracle_mod, 1, 3)
+    plan = tb.Plan.from_circuit(c)
+    assert plan.info["boundary_bits"] == 33
+    ref = oracle_mod.closed_form_hdiag(c, bits)
+    assert rel_l2(plan.amplitudes(bits), ref) < TOL
