@@ -86,9 +86,15 @@ __device__ __forceinline__ uint32_t run_base(int r, uint32_t tid) {
 // lanes of a half warp then hit 16 different 8-byte bank pairs (runs >= 3,
 // 8-byte accesses), and for run 0, read as 16-byte pairs, the 8 lanes of a
 // quarter warp hit 8 different 16-byte bank groups.
-__device__ __forceinline__ uint32_t swz(uint32_t idx) {
+__host__ __device__ __forceinline__ constexpr uint32_t swz(uint32_t idx) {
     return idx ^ (((idx >> 6) & 1u) << 1) ^ (((idx >> 7) & 1u) << 2) ^ ((((idx >> 5) ^ (idx >> 8)) & 1u) << 3);
 }
+// swz is linear over GF(2): for disjoint bit sets, swz(a | b) = swz(a) ^ swz(b),
+// so a run's 32 slots are the thread's swizzled base XOR compile-time constants.
+template <uint32_t J>
+struct SwzC {
+    static constexpr uint32_t v = swz(J);
+};
 
 
 // ---------------------------------------------------------------------------
@@ -236,49 +242,64 @@ __device__ __forceinline__ void stage_coefficients(const StepG* steps, float2* s
 // Registers <-> shared tile for register run R (entry j = k + 16 v at tile
 // coordinate base | j << R). Run 0 moves the two entries of a 16-byte chunk
 // in one 16-byte access.
+template <int R, int J>
+__device__ __forceinline__ uint32_t run_slot(uint32_t sb) {
+    return sb ^ SwzC<((uint32_t)J << R)>::v;
+}
+
+template <int R, int J>
+__device__ __forceinline__ void smem_read_run(float2 (&P)[16], float2 (&Q)[16], const float2* tile, uint32_t sb) {
+    if constexpr (J < 32) {
+        const float2 e = tile[run_slot<R, J>(sb)];
+        if constexpr (J < 16) { P[J].x = e.x; Q[J].x = e.y; }
+        else                  { P[J - 16].y = e.x; Q[J - 16].y = e.y; }
+        smem_read_run<R, J + 1>(P, Q, tile, sb);
+    }
+}
+
+template <int R, int J>
+__device__ __forceinline__ void smem_write_run(const float2 (&P)[16], const float2 (&Q)[16], float2* tile, uint32_t sb) {
+    if constexpr (J < 32) {
+        tile[run_slot<R, J>(sb)] = J < 16 ? make_float2(P[J & 15].x, Q[J & 15].x) : make_float2(P[J & 15].y, Q[J & 15].y);
+        smem_write_run<R, J + 1>(P, Q, tile, sb);
+    }
+}
+
 template <int R>
 __device__ __forceinline__ void smem_read(float2 (&P)[16], float2 (&Q)[16], const float2* tile, uint32_t tid) {
-    uint32_t b = run_base(R, tid);
-    asm volatile("" : "+r"(b));
-#pragma unroll
-    for (int v = 0; v < 2; ++v) {
-        if constexpr (R == 0) {
-#pragma unroll
-            for (int k = 0; k < 16; k += 2) {
-                const float4 e = *reinterpret_cast<const float4*>(tile + swz(b | (uint32_t)(k + 16 * v)));
-                if (v == 0) { P[k].x = e.x; Q[k].x = e.y; P[k + 1].x = e.z; Q[k + 1].x = e.w; }
-                else        { P[k].y = e.x; Q[k].y = e.y; P[k + 1].y = e.z; Q[k + 1].y = e.w; }
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const float2 e = tile[swz(b | ((uint32_t)(k + 16 * v) << R))];
-                if (v == 0) { P[k].x = e.x; Q[k].x = e.y; }
-                else        { P[k].y = e.x; Q[k].y = e.y; }
-            }
-        }
+    uint32_t sb = swz(run_base(R, tid));
+    asm volatile("" : "+r"(sb));
+    if constexpr (R == 0) {
+#define TB_RD0(K, V)                                                                                         \
+    {                                                                                                        \
+        const float4 e = *reinterpret_cast<const float4*>(tile + run_slot<0, (K) + 16 * (V)>(sb));         \
+        if ((V) == 0) { P[K].x = e.x; Q[K].x = e.y; P[(K) + 1].x = e.z; Q[(K) + 1].x = e.w; }              \
+        else          { P[K].y = e.x; Q[K].y = e.y; P[(K) + 1].y = e.z; Q[(K) + 1].y = e.w; }              \
+    }
+        TB_RD0(0, 0) TB_RD0(2, 0) TB_RD0(4, 0) TB_RD0(6, 0) TB_RD0(8, 0) TB_RD0(10, 0) TB_RD0(12, 0) TB_RD0(14, 0)
+        TB_RD0(0, 1) TB_RD0(2, 1) TB_RD0(4, 1) TB_RD0(6, 1) TB_RD0(8, 1) TB_RD0(10, 1) TB_RD0(12, 1) TB_RD0(14, 1)
+#undef TB_RD0
+    } else {
+        smem_read_run<R, 0>(P, Q, tile, sb);
     }
 }
 
 template <int R>
 __device__ __forceinline__ void smem_write(const float2 (&P)[16], const float2 (&Q)[16], float2* tile, uint32_t tid) {
-    uint32_t b = run_base(R, tid);
-    asm volatile("" : "+r"(b));
-#pragma unroll
-    for (int v = 0; v < 2; ++v) {
-        if constexpr (R == 0) {
-#pragma unroll
-            for (int k = 0; k < 16; k += 2) {
-                const float4 e = v == 0 ? make_float4(P[k].x, Q[k].x, P[k + 1].x, Q[k + 1].x)
-                                        : make_float4(P[k].y, Q[k].y, P[k + 1].y, Q[k + 1].y);
-                *reinterpret_cast<float4*>(tile + swz(b | (uint32_t)(k + 16 * v))) = e;
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < 16; ++k)
-                tile[swz(b | ((uint32_t)(k + 16 * v) << R))] =
-                    v == 0 ? make_float2(P[k].x, Q[k].x) : make_float2(P[k].y, Q[k].y);
-        }
+    uint32_t sb = swz(run_base(R, tid));
+    asm volatile("" : "+r"(sb));
+    if constexpr (R == 0) {
+#define TB_WR0(K, V)                                                                                          \
+    {                                                                                                         \
+        const float4 e = (V) == 0 ? make_float4(P[K].x, Q[K].x, P[(K) + 1].x, Q[(K) + 1].x)                   \
+                                  : make_float4(P[K].y, Q[K].y, P[(K) + 1].y, Q[(K) + 1].y);                  \
+        *reinterpret_cast<float4*>(tile + run_slot<0, (K) + 16 * (V)>(sb)) = e;                              \
+    }
+        TB_WR0(0, 0) TB_WR0(2, 0) TB_WR0(4, 0) TB_WR0(6, 0) TB_WR0(8, 0) TB_WR0(10, 0) TB_WR0(12, 0) TB_WR0(14, 0)
+        TB_WR0(0, 1) TB_WR0(2, 1) TB_WR0(4, 1) TB_WR0(6, 1) TB_WR0(8, 1) TB_WR0(10, 1) TB_WR0(12, 1) TB_WR0(14, 1)
+#undef TB_WR0
+    } else {
+        smem_write_run<R, 0>(P, Q, tile, sb);
     }
 }
 
@@ -374,16 +395,19 @@ __device__ __forceinline__ int64_t tile_origin(int64_t t, int lo) {
 
 // Issue the 16-byte copies of tile gt into a stage (4096 chunks, 16 per thread;
 // chunk c = j*256 + tid covers tile coordinates 2c, 2c+1).
+// Chunk c = j*256 + tid: tile coordinate 2*tid + 512*j. The two terms have
+// disjoint bits, so the swizzled slot is swz(2*tid) + 512*j and the HBM offset
+// is tile_addr(2*tid) + tile_addr(512*j) (a per-thread base plus constants).
 template <class SH>
-__device__ __forceinline__ void issue_tile(const PassParams& p, int64_t gt, float2* stage, uint32_t tid) {
+__device__ __forceinline__ void issue_tile(const PassParams& p, int64_t gt, float2* stage, uint32_t s0,
+                                           int64_t a0) {
     const int64_t b = gt >> p.tile_shift;
     const int64_t t = gt & (((int64_t)1 << p.tile_shift) - 1);
-    const float2* base = p.B + b * p.b_stride + tile_origin<SH>(t, p.lo);
+    const float2* base = p.B + b * p.b_stride + tile_origin<SH>(t, p.lo) + a0;
+    const int64_t st = tile_addr<SH>(2u * PASS_THREADS, p.lo);  // HBM offset of j = 1
 #pragma unroll
-    for (int j = 0; j < TILE / 2 / PASS_THREADS; ++j) {
-        const uint32_t idx = 2u * ((uint32_t)j * PASS_THREADS + tid);
-        cp_async16(stage + swz(idx), base + tile_addr<SH>(idx, p.lo));
-    }
+    for (int j = 0; j < TILE / 2 / PASS_THREADS; ++j)
+        cp_async16(stage + s0 + 2u * PASS_THREADS * j, base + j * st);
 }
 
 
@@ -399,11 +423,14 @@ __global__ void __launch_bounds__(PASS_THREADS, PASS_CTAS_PER_SM) pass_kernel(co
 
     stage_coefficients<SH>(p.steps, sc, tid);
 
+    // per-thread parts of the tile copy addresses (see issue_tile)
+    const uint32_t cs0 = swz(2u * tid);
+    const int64_t ca0 = tile_addr<SH>(2u * tid, p.lo);
     // prologue: the first PASS_STAGES-1 tiles of this CTA
 #pragma unroll
     for (int s = 0; s < PASS_STAGES - 1; ++s) {
         const int64_t gt = blockIdx.x + (int64_t)s * gridDim.x;
-        if (gt < p.ntiles) issue_tile<SH>(p, gt, smem + s * TILE, tid);
+        if (gt < p.ntiles) issue_tile<SH>(p, gt, smem + s * TILE, cs0, ca0);
         cp_async_commit();
     }
 
@@ -418,7 +445,7 @@ __global__ void __launch_bounds__(PASS_THREADS, PASS_CTAS_PER_SM) pass_kernel(co
         {   // keep PASS_STAGES-1 tiles in flight
             const int64_t nx = gt + (int64_t)(PASS_STAGES - 1) * gridDim.x;
             const int ns = (stage + PASS_STAGES - 1) % PASS_STAGES;
-            if (nx < p.ntiles) issue_tile<SH>(p, nx, smem + ns * TILE, tid);
+            if (nx < p.ntiles) issue_tile<SH>(p, nx, smem + ns * TILE, cs0, ca0);
             cp_async_commit();
         }
         const int64_t b = gt >> p.tile_shift;
