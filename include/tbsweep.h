@@ -363,6 +363,17 @@ TB_API const char* tb_last_error(void);
  * Returns TB_OK, TB_EINVAL (NULL count) or TB_ECUDA. */
 TB_API int tb_device_faults(int32_t* count);
 
+/* Self-test of the bounded device waits (no counterpart in the paper): one
+ * small split-precision evaluation (n = 3, d = 26, 3xBF16) whose tensor-core
+ * kernels wait for MMAs that are never issued. Each wait gives up after a
+ * short bounded number of tries and is counted; the kernels stop, release
+ * their tensor memory and exit, so the device stays usable (nothing faults or
+ * hangs). *faults receives the number of waits that gave up (positive when the
+ * mechanism works); the result of that evaluation is discarded. Allocates and
+ * frees a small workspace; synchronises the device. Returns TB_OK, TB_EINVAL
+ * (NULL faults) or TB_ECUDA. */
+TB_API int tb_selftest_bounded_wait(int32_t* faults);
+
 #ifdef __cplusplus
 }
 #endif

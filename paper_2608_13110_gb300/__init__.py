@@ -74,6 +74,7 @@ _sig = {
     "tb_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "tb_last_error": (ctypes.c_char_p, []),
     "tb_device_faults": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32)]),
+    "tb_selftest_bounded_wait": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32)]),
     "tb_plan_create_open": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _u8p, _u8p, ctypes.POINTER(_Gate1q),
                                            ctypes.c_int, ctypes.POINTER(_Opts), ctypes.c_int,
                                            ctypes.POINTER(_vp)]),
@@ -188,6 +189,14 @@ def sample(plan, n_samples: int, rng, ws=None):
     for j in range(k):
         bits[:, plan.n - k + j] = (b >> j) & 1
     return bits, amps[np.arange(int(n_samples)), b], q
+
+
+def selftest_bounded_wait() -> int:
+    """Run a small evaluation whose device waits are made to run out on
+    purpose (see tb_selftest_bounded_wait); returns how many gave up."""
+    c = ctypes.c_int32()
+    _check(_lib.tb_selftest_bounded_wait(ctypes.byref(c)), "tb_selftest_bounded_wait")
+    return int(c.value)
 
 
 def device_faults() -> int:

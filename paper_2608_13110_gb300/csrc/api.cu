@@ -78,6 +78,9 @@ struct ProfScope {
 
 bool small_path(const Plan& P) { return P.h <= SMALL_H_MAX; }
 
+// Set by tb_selftest_bounded_wait for the evaluation it runs on this thread.
+thread_local bool t_tc_selftest = false;
+
 CallLayout call_layout(const Plan& P) {
     CallLayout c;
     if (small_path(P)) return c;
@@ -224,6 +227,7 @@ int run_device(const Plan& P, const uint8_t* d_bits, int64_t nb, void* d_ws, int
                 tp.sstride = sstride;
                 tp.slot = (int)k;
                 tp.fault = fault;
+                tp.selftest = t_tc_selftest ? 1 : 0;
                 const int grid = (int)std::min<int64_t>(tp.ntiles, (int64_t)TC_CTAS_PER_SM * nsm);
                 ProfScope ps(PC_PASS, 16.0 * (double)nbat * (double)b_stride, st);
                 TB_CUDA(launch_tc_pass(P.opts.precision, tp, grid, st));
@@ -553,6 +557,38 @@ int tb_profile_end(tb_profile_t* out) {
     g_prof.recs.clear();
     g_prof.used = 0;
     return TB_OK;
+}
+
+int tb_selftest_bounded_wait(int32_t* faults) {
+    if (!faults) return fail(TB_EINVAL, "faults is NULL");
+    *faults = 0;
+    tb_opts o;
+    std::memset(&o, 0, sizeof(o));
+    o.precision = TB_PRECISION_BF16X3;
+    tb_plan* plan = nullptr;
+    int rc = tb_plan_create(3, 26, nullptr, nullptr, nullptr, 0, &o, &plan);
+    if (rc != TB_OK) return rc;
+    int32_t before = 0;
+    rc = tb_device_faults(&before);  // clears the word
+    void* ws = nullptr;
+    double* out = nullptr;
+    uint8_t* bits = nullptr;
+    const int64_t wsb = tb_workspace_bytes(plan, 1);
+    if (rc == TB_OK && (cudaMalloc(&ws, (size_t)wsb) != cudaSuccess || cudaMalloc(&out, 16) != cudaSuccess ||
+                        cudaMalloc(&bits, 3) != cudaSuccess || cudaMemset(bits, 0, 3) != cudaSuccess))
+        rc = fail(TB_ECUDA, "self-test allocation failed");
+    if (rc == TB_OK) rc = tb_plan_upload(plan, ws, wsb, nullptr);
+    if (rc == TB_OK) {
+        t_tc_selftest = true;
+        rc = run_device(plan->p, bits, 1, ws, wsb, plan->p.lay.total, out, nullptr);
+        t_tc_selftest = false;
+    }
+    if (rc == TB_OK) rc = tb_device_faults(faults);
+    cudaFree(bits);
+    cudaFree(out);
+    cudaFree(ws);
+    tb_plan_destroy(plan);
+    return rc;
 }
 
 int tb_device_faults(int32_t* count) {

@@ -25,6 +25,7 @@ struct TcParams {
     int64_t sstride;
     int slot;               // slot read; slot+1 written
     int* fault;             // incremented when a bounded wait gives up
+    int selftest;           // 1: issue no MMA and give up waiting after a few tries (tests the bounded waits)
 };
 
 // precision: TB_PRECISION_TF32X3 or TB_PRECISION_BF16X3.

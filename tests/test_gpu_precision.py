@@ -120,3 +120,17 @@ def test_narrow_plans_use_the_fp32_kernel(tb):
     p = tb.Plan.from_circuit(c, precision="bf16x3")
     assert p.info["n_passes"] == 0
     np.testing.assert_array_equal(p.amplitudes(c.bits), tb.Plan.from_circuit(c).amplitudes(c.bits))
+
+
+def test_bounded_waits_give_up_and_the_device_stays_usable(tb):
+    """Failure detection without a fault: the self-test evaluation waits for
+    MMAs that are never issued; every wait gives up after its bounded number
+    of tries, is counted, and the kernels free their tensor memory and exit.
+    Afterwards the same kernels run normally on the same context."""
+    assert tb.selftest_bounded_wait() > 0
+    assert tb.device_faults() == 0  # the self-test read and cleared the count
+    c = W.random_circuit(9, 28, None, 8, 77)
+    ref = tb.Plan.from_circuit(c).amplitudes(c.bits)
+    got = tb.Plan.from_circuit(c, precision="bf16x3").amplitudes(c.bits)
+    assert rel_l2(got, ref) < BOUND["bf16x3"]
+    assert tb.device_faults() == 0
