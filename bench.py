@@ -220,7 +220,13 @@ def run_ours(args, rank, world, local):
         c = W.random_circuit(n_, d_, None, nb, 4000 + 100 * rank + d_)
     else:
         c = W.precision_70_64(replica=rank, nb=nb)
-    plan = tb.Plan.from_circuit(c, precision=args.precision)
+    sched_opts = {}
+    if args.precision == "fp32" and not args.default_schedule:
+        from paper_2608_13110_gb300 import autotune
+        t_tune = time.perf_counter()
+        sched_opts = autotune.tune(c.d // 2, nb)
+        t_tune = time.perf_counter() - t_tune
+    plan = tb.Plan.from_circuit(c, precision=args.precision, **sched_opts)
     info = plan.info
     h = info["boundary_bits"]
     ws = torch.empty(plan.workspace_bytes(nb), dtype=torch.uint8, device=dev)
@@ -287,6 +293,8 @@ def run_ours(args, rank, world, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "complex64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": 70, "d": 64, "n_t": 426, "bitstrings_per_step": nb,
                    "pass_arithmetic": args.precision,
+                   "schedule": ({"autotuned": sched_opts, "tune_s": round(t_tune, 1)} if sched_opts
+                                else "planner default"),
                    "width": info["width"], "passes_per_amplitude": info["n_passes"],
                    "l2": "inputs larger than L2 (32 GiB boundary, 129 MB L2)",
                    "parallelism": f"replicas x{world}"},
@@ -421,8 +429,10 @@ def run_precision_workload(args, rank, world, local):
     forms = {}
     ref_amps = None
     clocks = ClockSampler(local)
+    from paper_2608_13110_gb300 import autotune
+    tuned = {} if args.default_schedule else autotune.tune(c.d // 2, 1)
     for form in ("fp32", "tf32x3", "bf16x3"):
-        plan = tb.Plan.from_circuit(c, precision=form)
+        plan = tb.Plan.from_circuit(c, precision=form, **(tuned if form == "fp32" else {}))
         ws = torch.empty(plan.workspace_bytes(nb), dtype=torch.uint8, device=dev)
         plan.upload(ws, stream)
         d_bits = torch.from_numpy(c.bits).to(dev)
@@ -468,6 +478,7 @@ def run_precision_workload(args, rank, world, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "complex64", "data": "synthetic",
             "config": {"workload": f"brickwork CZ n=70 d=64, random Cliffords, 426 T, {nb} bitstrings/step, "
                                    "width 32; value = the plain FP32 form",
+                       "fp32_schedule": {"autotuned": tuned} if tuned else "planner default",
                        "l2": "inputs larger than L2 (32 GiB boundary)", "parallelism": f"replicas x{world}",
                        "peak_hbm_gbs": hbm_peak},
             "forms": forms, "clocks": clk}
@@ -494,7 +505,11 @@ def run_open_workload(args, rank, world, local):
         c = W.precision_70_64(replica=rank, nb=1)
     rng = np.random.default_rng(7000 + rank)
     prefixes = rng.integers(0, 2, size=(na, c.n - k), dtype=np.uint8)
-    plan = tb.Plan.from_circuit(c, open_k=k, precision=args.precision)
+    sched_opts = {}
+    if args.precision == "fp32" and not args.default_schedule:
+        from paper_2608_13110_gb300 import autotune
+        sched_opts = autotune.tune(c.d // 2, 1)
+    plan = tb.Plan.from_circuit(c, open_k=k, precision=args.precision, **sched_opts)
     info = plan.info
     stream = torch.cuda.current_stream(dev)
     ws = torch.empty(plan.workspace_bytes(na), dtype=torch.uint8, device=dev)
@@ -531,7 +546,7 @@ def run_open_workload(args, rank, world, local):
     bits[:, : c.n - k] = prefixes[0]
     for j in range(k):
         bits[:, c.n - k + j] = (ys >> j) & 1
-    pplan = tb.Plan.from_circuit(c, precision=args.precision)
+    pplan = tb.Plan.from_circuit(c, precision=args.precision, **sched_opts)
     pws = torch.empty(pplan.workspace_bytes(4), dtype=torch.uint8, device=dev)
     pplan.upload(pws, stream)
     d_bits = torch.from_numpy(bits).to(dev)
@@ -554,6 +569,7 @@ def run_open_workload(args, rank, world, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "complex64", "data": "synthetic",
             "config": {"workload": f"brickwork CZ {shape}, random Cliffords, {c.n_t} T, k=8, {na} uniform prefixes/step",
                        "open_k": k, "open_width": info["open_width"], "passes_per_prefix": info["n_passes"],
+                       "schedule": {"autotuned": sched_opts} if sched_opts else "planner default",
                        "pass_arithmetic": args.precision, "parallelism": f"replicas x{world}"},
             "e2e": {"value": world * na * (1 << k) / t_e2e, "unit": UNIT,
                     "h2d_bytes_per_step": int(prefixes.nbytes + info["table_bytes"]),
@@ -656,6 +672,8 @@ def main():
     ap.add_argument("--nb-open", type=int, default=2, help="prefixes per step in the open workload")
     ap.add_argument("--precision", default="fp32", choices=("fp32", "tf32x3", "bf16x3"),
                     help="pass arithmetic of the n70d64 workload")
+    ap.add_argument("--default-schedule", action="store_true",
+                    help="use the planner's default window schedule instead of the autotuned one")
     ap.add_argument("--nb-precision", type=int, default=4, help="bitstrings per step in the precision workload")
     ap.add_argument("--requests", type=int, default=200, help="requests in the serve workload")
     ap.add_argument("--shape", default="", help="n,d of a smaller circuit (profiling only; not the reported workload)")

@@ -77,11 +77,22 @@ def candidate_options(h: int, n_rows: int = 8, limit: int = 8) -> list[dict]:
     return [default] + ranked[: max(0, limit - 1)]
 
 
+# Boundary entries the device keeps in flight per call by default (8 GiB of
+# complex64): wider boundaries are evaluated one bitstring after another, so
+# timing more of them measures nothing new.
+BATCH_ENTRIES = 1 << 30
+
+
 def measure(opts: dict, h: int, nb: int, n_rows: int = 8, reps: int = 3, seed: int = 1) -> float:
     """Milliseconds per batch of nb amplitudes of an (n_rows+2)-qubit circuit
-    of width h under the given window options (median of reps)."""
+    of width h under the given window options (median of reps). A batch
+    larger than the device evaluates at once is timed on the part it runs
+    concurrently and scaled."""
     import torch
     import workloads as W
+    run = max(1, min(nb, BATCH_ENTRIES >> h))
+    scale = nb / run
+    nb = run
     c = W.random_circuit(n_rows + 2, 2 * h, None, nb, seed)
     plan = Plan.from_circuit(c, **opts)
     ws = plan.alloc_workspace(nb)
@@ -99,13 +110,22 @@ def measure(opts: dict, h: int, nb: int, n_rows: int = 8, reps: int = 3, seed: i
         e1.record()
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
-    return float(np.median(times))
+    return float(np.median(times)) * scale
 
 
-def tune(h: int, nb: int = 1, n_rows: int = 8, limit: int = 8, use_cache: bool = True) -> dict:
-    """Fastest window options for width h with nb bitstrings side by side."""
+WIDE_LIMIT = 24  # candidates timed for boundaries of at least 2^WIDE_H entries
+WIDE_H = 26
+
+
+def tune(h: int, nb: int = 1, n_rows: int = 8, limit: int = 0, use_cache: bool = True) -> dict:
+    """Fastest window options for width h with nb bitstrings side by side.
+    limit = 0 times 8 candidates, or 24 for widths >= 26: there the address
+    span of a window changes the pass time (page and DRAM locality), which the
+    planner's arithmetic cost model does not see."""
     if h <= NARROW_MAX_WIDTH:
         return {"window_bits": 0, "bottom_bits": 0, "top_bits": 0}
+    if limit <= 0:
+        limit = WIDE_LIMIT if h >= WIDE_H else 8
     import torch
     key = f"{torch.cuda.get_device_name()}|h={h}|nb={_bucket(nb)}"
     with _LOCK:
