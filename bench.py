@@ -496,7 +496,7 @@ def run_open_workload(args, rank, world, local):
     import paper_2608_13110_gb300 as tb
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    k = 8
+    k = args.open_k
     na = args.nb_open
     if args.shape:  # profiling aid: a smaller circuit with the same statistics
         n_, d_ = (int(v) for v in args.shape.split(","))
@@ -541,7 +541,7 @@ def run_open_workload(args, rank, world, local):
     plan.amplitudes(pre_pin.numpy(), ws=ws, stream=stream, out=out_pin.numpy())
     t_e2e = max_over_ranks(time.perf_counter() - t0, world, dev)
     # the plain sweep on four of the same bitstrings, for the comparison and a cross-check
-    ys = np.array([0, 77, 200, 255])
+    ys = np.array([0, 77, 200, 255]) % (1 << k)
     bits = np.zeros((4, c.n), np.uint8)
     bits[:, : c.n - k] = prefixes[0]
     for j in range(k):
@@ -563,11 +563,11 @@ def run_open_workload(args, rank, world, local):
     b, q = tb.batched_sample(amps, rng.random(na))
     total = max(1e-9, sum(v["ms"] for v in prof.values()))
     shape = f"n={c.n}, d={c.d}" + (" (--shape, profiling)" if args.shape else "")
-    line = {"metric": f"amplitudes/s ({shape}, k=8 open output bits: 256 amplitudes per sweep)",
+    line = {"metric": f"amplitudes/s ({shape}, k={k} open output bits: {1 << k} amplitudes per sweep)",
             "value": world * na * (1 << k) * args.steps / t, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "complex64", "data": "synthetic",
-            "config": {"workload": f"brickwork CZ {shape}, random Cliffords, {c.n_t} T, k=8, {na} uniform prefixes/step",
+            "config": {"workload": f"brickwork CZ {shape}, random Cliffords, {c.n_t} T, k={k}, {na} uniform prefixes/step",
                        "open_k": k, "open_width": info["open_width"], "passes_per_prefix": info["n_passes"],
                        "schedule": {"autotuned": sched_opts} if sched_opts else "planner default",
                        "pass_arithmetic": args.precision, "parallelism": f"replicas x{world}"},
@@ -670,6 +670,7 @@ def main():
                          "precision: FP32 vs 3xTF32 / 3xBF16 tensor-core passes with errors vs FP64; "
                          "open: Algorithm 2, 256 amplitudes per sweep (k=8)")
     ap.add_argument("--nb-open", type=int, default=2, help="prefixes per step in the open workload")
+    ap.add_argument("--open-k", type=int, default=8, help="open output bits in the open workload (1..10)")
     ap.add_argument("--precision", default="fp32", choices=("fp32", "tf32x3", "bf16x3"),
                     help="pass arithmetic of the n70d64 workload")
     ap.add_argument("--default-schedule", action="store_true",
