@@ -586,7 +586,9 @@ def run_open_workload(args, rank, world, local):
 
 def run_serve_workload(args, rank, world, local):
     """Poisson stream (mean 20 requests/s) of amplitude requests, n ~ U[16,70],
-    d even ~ U{8..44} (width <= 22), 1..256 bitstrings each,
+    d even ~ U{8..44} (width <= 22: a width-33 request of 256 bitstrings alone
+    needs about 35 GPU-minutes, so the full d <= 66 range cannot be served at
+    20 requests/s by one GPU), 1..256 bitstrings each,
     through the serving runtime (160 GB budget, continuous admission) against
     the plain path: the same requests one at a time in arrival order."""
     import threading
