@@ -39,12 +39,20 @@ def _load_cache() -> dict:
 
 
 def _save_cache(c: dict) -> None:
+    """Best effort: an unwritable cache only costs re-tuning later. Each
+    process writes its own temporary file, then renames it into place."""
     p = cache_path()
-    os.makedirs(os.path.dirname(p), exist_ok=True)
-    tmp = p + ".tmp"
-    with open(tmp, "w") as f:
-        json.dump(c, f, indent=1, sort_keys=True)
-    os.replace(tmp, p)
+    tmp = f"{p}.{os.getpid()}.tmp"
+    try:
+        os.makedirs(os.path.dirname(p) or ".", exist_ok=True)
+        with open(tmp, "w") as f:
+            json.dump(c, f, indent=1, sort_keys=True)
+        os.replace(tmp, p)
+    except OSError:
+        try:
+            os.remove(tmp)
+        except OSError:
+            pass
 
 
 def _bucket(nb: int) -> int:
