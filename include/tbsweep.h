@@ -63,10 +63,10 @@ typedef struct {
 } tb_gate1q;
 
 /* Pass arithmetic (tb_opts.precision). The split forms compose several
- * paired steps into a dense block so that tensor cores can apply them; the
- * paper merges small branch tensors before contracting them with the
- * boundary (Sec. 5.2) and evaluates the precision of complex64 against
- * complex128 (Sec. 5.1). */
+ * paired steps into a dense block so that tensor cores can apply them (the
+ * paper's production code also combines small tensors before the boundary
+ * contraction, Sec. 5.2, and compares complex64 with complex128 precision,
+ * Sec. 5.1). */
 enum {
     TB_PRECISION_FP32 = 0,
     TB_PRECISION_TF32X3 = 1,

@@ -1,8 +1,9 @@
 // Fused staircase pass over the temporal boundary (arXiv 2608.13110,
 // Sec. 3.1, Algorithm 1: every paired step contracts two row tensors into the
-// boundary; Sec. 5.2 merges small branch tensors before they touch the large
-// boundary, which here becomes: apply every step of one window of address
-// bits in a single read + write of the boundary).
+// boundary). As in the paper's production code (Sec. 5.2), where several small
+// tensors are combined first so that the big boundary is touched less often,
+// every step of one window of address bits is applied in a single read + write
+// of the boundary.
 //
 // A pass applies a compile-time sequence of controlled 2x2 steps to every
 // tile of 2^13 complex64 entries: the window's M address bits plus 13-M low

@@ -4,9 +4,10 @@
 // The paired steps of one absorbed row form a staircase of controlled 2x2
 // gates on consecutive address bits (Algorithm 1, paired contraction). A run
 // of steps whose targets and controls stay inside WB consecutive address bits
-// composes into one 2^WB x 2^WB complex matrix (the paper's Sec. 5.2 merges
-// small branch tensors before contracting them with the boundary; here the
-// merged tensor is a dense block applied by tensor cores). This file cuts
+// composes into one 2^WB x 2^WB complex matrix (in the paper's production
+// code, Sec. 5.2, small tensors are likewise combined ahead of the boundary
+// contraction; here the combined tensor is a dense block applied by tensor
+// cores). This file cuts
 // every row into such runs, composes each run in FP64, embeds it as a real
 // 2^(WB+1) x 2^(WB+1) matrix, splits it into a high and a low part in the
 // tensor-core operand format, and lays both out as the K-major shared-memory
