@@ -172,7 +172,7 @@ def batched_sample(amps, u):
 
 def sample(plan, n_samples: int, rng, ws=None):
     """Batched sampling (Sec. 4) with an open plan (``open_k = k``): draw
-    n_samples prefixes a uniformly from {0,1}^(n-k), evaluate the 2^k
+    n_samples uniform prefixes a in {0,1}^(n-k), evaluate the 2^k
     amplitudes of each on the device (one sweep per prefix), and draw one
     suffix b per prefix from p(b | a) = |<a,b|U|0^n>|^2 / Q_a. ``rng`` is a
     numpy Generator (the prefixes and the uniform variates come from it).

@@ -2,7 +2,7 @@
 //
 // Builds, in FP64, everything the device needs for one circuit:
 //   * the folded one-qubit gates U_(q,t) = E . T^tau . C (Sec. 2.1 / 2.2:
-//     one-qubit gates are absorbed into the neighbouring tensors);
+//     every one-qubit gate folds into a neighbouring tensor);
 //   * the paired steps of every absorbed row 1..n-2 (Algorithm 1's paired
 //     contraction of two row tensors with the boundary, Proposition 1 case (a))
 //     as controlled 2x2 gates on the boundary's address bits;

@@ -71,7 +71,7 @@ def test_cz_counts_of_the_brickwork_convention():
 
 def test_plan_topology_independent_of_gate_values(tb):
     """Width, cost, step and pass counts do not depend on the one-qubit gates
-    or on the number and placement of T gates (Sec. 1 contributions, Sec. 3.1)."""
+    nor on how many T gates there are or where they sit (Sec. 1 contributions, Sec. 3.1)."""
     c = W.precision_70_64(nb=1)
     a = tb.Plan.from_circuit(c).info
     b = tb.Plan.from_circuit(c.clifford_twin()).info
