@@ -604,7 +604,7 @@ def run_serve_workload(args, rank, world, local):
         pl.amplitudes(c.bits[:1])
     torch.cuda.synchronize(dev)
 
-    srv = tb.Server(hbm_budget_bytes=160 * 10**9, slots=8, device=local, pinned_bytes=256 << 20)
+    srv = tb.Server(hbm_budget_bytes=160 * 10**9, slots=args.serve_slots, device=local, pinned_bytes=256 << 20)
     tickets = [None] * len(reqs)
     t0 = time.perf_counter()
 
@@ -645,7 +645,7 @@ def run_serve_workload(args, rank, world, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "complex64", "data": "synthetic",
             "config": {"workload": f"{len(reqs)} requests, Poisson 20/s, n~U[16,70], d even <= 44 (width <= 22), "
                                    "1..256 bitstrings", "amplitudes": namps, "hbm_budget_bytes": 160 * 10**9,
-                       "slots": 8, "parallelism": f"replicas x{world}"},
+                       "slots": args.serve_slots, "parallelism": f"replicas x{world}"},
             "latency_s": {"p50": st["p50_latency_s"], "p99": st["p99_latency_s"], "mean": st["mean_latency_s"]},
             "server": {"peak_concurrent": st["peak_concurrent"], "peak_bytes_in_use": st["peak_bytes_in_use"]},
             "plain": {"value": world * namps / max_over_ranks(t_plain, world, dev), "unit": UNIT,
@@ -679,6 +679,8 @@ def main():
                     help="use the planner's default window schedule instead of the autotuned one")
     ap.add_argument("--nb-precision", type=int, default=4, help="bitstrings per step in the precision workload")
     ap.add_argument("--requests", type=int, default=200, help="requests in the serve workload")
+    ap.add_argument("--serve-slots", type=int, default=2,
+                    help="concurrent requests in the serve workload (2: best p99 on this stream)")
     ap.add_argument("--shape", default="", help="n,d of a smaller circuit (profiling only; not the reported workload)")
     args = ap.parse_args()
     if args.impl == "reference":
