@@ -265,3 +265,28 @@ def test_batched_sampling_tv_identity(oracle_mod):
     q = pk / (A * Q[None, :])
     tv = 0.5 * np.abs(q - pk).sum()
     assert abs(tv - 0.5 * np.abs(Q - 1.0 / A).sum()) < 1e-12
+
+
+def test_autotuner_measures_what_the_device_runs_at_once(tb, monkeypatch):
+    """Wide boundaries are evaluated one at a time, so the tuner times the
+    part of the batch the device holds and scales it; wide widths try more
+    candidates (window placement matters there)."""
+    from paper_2608_13110_gb300 import autotune
+    seen = []
+
+    def fake_measure(opts, h, nb, n_rows=8, reps=3, seed=1):
+        seen.append((h, nb))
+        return float(opts["window_bits"] or 11)
+
+    import torch
+    monkeypatch.setattr(autotune, "measure", fake_measure)
+    monkeypatch.setattr(torch.cuda, "get_device_name", lambda *a: "no device (host test)")
+    monkeypatch.setenv("TB_AUTOTUNE_CACHE", "/nonexistent/dir/tune.json")  # unwritable: best effort
+    best = autotune.tune(32, nb=16, use_cache=False)
+    assert len(seen) == autotune.WIDE_LIMIT and all(h == 32 for h, _ in seen)
+    assert best["window_bits"] == min(o["window_bits"] for o in autotune.candidate_options(32, limit=24)
+                                      if o["window_bits"])
+    seen.clear()
+    autotune.tune(20, nb=16, use_cache=False)
+    assert len(seen) == 8
+    assert autotune.BATCH_ENTRIES >> 32 == 0  # one width-32 boundary at a time

@@ -134,3 +134,30 @@ def test_bounded_waits_give_up_and_the_device_stays_usable(tb):
     got = tb.Plan.from_circuit(c, precision="bf16x3").amplitudes(c.bits)
     assert rel_l2(got, ref) < BOUND["bf16x3"]
     assert tb.device_faults() == 0
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+def test_maximum_width_33(tb, oracle_mod, prec):
+    """Width 33 (64 GiB boundary) with tensor-core passes, closed form."""
+    from test_gpu_parity import _nonzero_bits
+    c = W.hdiag_circuit(70, 66, 439, 0, 4300)
+    bits = _nonzero_bits(c, oracle_mod, 1, 3)
+    ref = oracle_mod.closed_form_hdiag(c, bits)
+    assert rel_l2(_amps(tb, c, bits, prec), ref) < BOUND[prec]
+
+
+def test_split_precision_plans_in_a_graph_batch(tb):
+    """The batch runtime records tensor-core passes like any other: a mixed
+    batch of FP32, 3xTF32 and 3xBF16 plans equals the single calls."""
+    import torch
+    circuits = [W.random_circuit(n, d, None, nb, 1800 + i)
+                for i, (n, d, nb) in enumerate([(10, 28, 3), (14, 30, 2), (9, 34, 4)])]
+    plans = [tb.Plan.from_circuit(c, precision=p) for c, p in zip(circuits, ("fp32", "tf32x3", "bf16x3"))]
+    d_bits = [torch.from_numpy(c.bits).cuda() for c in circuits]
+    d_out = [torch.empty((c.bits.shape[0], 2), dtype=torch.float64, device="cuda") for c in circuits]
+    batch = tb.Batch(list(zip(plans, d_bits, d_out)))
+    batch.launch()
+    torch.cuda.synchronize()
+    for c, p, o in zip(circuits, plans, d_out):
+        got = o.cpu().numpy().view(np.complex128).reshape(-1)
+        np.testing.assert_array_equal(got, p.amplitudes(c.bits))
