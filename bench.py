@@ -202,7 +202,7 @@ def run_reference(args, rank, world):
             "steps": steps, "warmup": warm, "ms_per_step": None, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "complex128", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": 70, "d": 64, "n_t": 426, "bitstrings_per_step": 16,
-                       "parallelism": "replicas"},
+                       "parallelism": f"replicas x{world}"},
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
