@@ -161,3 +161,23 @@ def test_split_precision_plans_in_a_graph_batch(tb):
     for c, p, o in zip(circuits, plans, d_out):
         got = o.cpu().numpy().view(np.complex128).reshape(-1)
         np.testing.assert_array_equal(got, p.amplitudes(c.bits))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "bf16x3"])
+@pytest.mark.parametrize("n,d", [(14, 26), (16, 30)])
+def test_total_variation_of_the_output_distribution(tb, oracle_mod, prec, n, d):
+    """Total variation between the output distributions of the GPU forms and
+    FP64 over every bitstring (the paper compares complex64 with complex128 this
+    way, Sec. 5.1). For unit vectors TV = 1/2 sum | |psi|^2 - |phi|^2 | <=
+    1/2 |psi - phi| |psi + phi| <= |psi - phi|, so the relative-L2 bound of each
+    form also bounds its TV."""
+    c = W.random_circuit(n, d, None, 0, 1900 + n)
+    x = np.arange(1 << n)
+    bits = ((x[:, None] >> np.arange(n)[None, :]) & 1).astype(np.uint8)
+    a = tb.Plan.from_circuit(c, precision=prec).amplitudes(bits)
+    psi = oracle_mod.sv_state(n, d, oracle_mod.circuit_gates(c))
+    tv = 0.5 * np.abs(np.abs(a) ** 2 - np.abs(psi) ** 2).sum()
+    err = float(np.linalg.norm(a - psi))
+    print(f"\nTV {prec} n={n} d={d}: {tv:.3e} (relative L2 {err:.3e})")
+    assert tv <= err * (1 + 1e-9) + 1e-15
+    assert err < (1e-5 if prec == "fp32" else BOUND[prec])
