@@ -224,7 +224,7 @@ def run_ours(args, rank, world, local):
     if args.precision == "fp32" and not args.default_schedule:
         from paper_2608_13110_gb300 import autotune
         t_tune = time.perf_counter()
-        sched_opts = autotune.tune(c.d // 2, nb)
+        sched_opts = autotune.tune((c.d + 1) // 2, nb)
         t_tune = time.perf_counter() - t_tune
     plan = tb.Plan.from_circuit(c, precision=args.precision, **sched_opts)
     info = plan.info
@@ -381,7 +381,7 @@ def run_batch_workload(args, rank, world, local):
             "warmup": args.warmup, "ms_per_step": 1e3 * t_b / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "complex64", "data": "synthetic",
             "config": {"workload": "64 circuits n~U[20,70], d~U{16..48} even, T density 0.095, 32 bitstrings each",
-                       "widths": sorted({c.d // 2 for c in circuits}), "autotune_s": tune_s,
+                       "widths": sorted({(c.d + 1) // 2 for c in circuits}), "autotune_s": tune_s,
                        "graph_record_s": record_s, "parallelism": f"replicas x{world}"},
             "plain": {"value": world * namps * args.steps / t_p, "unit": UNIT, "ms_per_step": 1e3 * t_p / args.steps,
                       "how": "one tb_amplitudes_device call per circuit, back to back on one stream"},
@@ -430,7 +430,7 @@ def run_precision_workload(args, rank, world, local):
     ref_amps = None
     clocks = ClockSampler(local)
     from paper_2608_13110_gb300 import autotune
-    tuned = {} if args.default_schedule else autotune.tune(c.d // 2, 1)
+    tuned = {} if args.default_schedule else autotune.tune((c.d + 1) // 2, 1)
     for form in ("fp32", "tf32x3", "bf16x3"):
         plan = tb.Plan.from_circuit(c, precision=form, **(tuned if form == "fp32" else {}))
         ws = torch.empty(plan.workspace_bytes(nb), dtype=torch.uint8, device=dev)
@@ -508,7 +508,7 @@ def run_open_workload(args, rank, world, local):
     sched_opts = {}
     if args.precision == "fp32" and not args.default_schedule:
         from paper_2608_13110_gb300 import autotune
-        sched_opts = autotune.tune(c.d // 2, 1)
+        sched_opts = autotune.tune((c.d + 1) // 2, 1)
     plan = tb.Plan.from_circuit(c, open_k=k, precision=args.precision, **sched_opts)
     info = plan.info
     stream = torch.cuda.current_stream(dev)

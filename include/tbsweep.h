@@ -9,7 +9,10 @@
  * still waits for its partner. Absorbing a row is a staircase of h paired
  * steps (consume one stored bit, create the next one), each a controlled 2x2
  * complex gate on two adjacent address bits; rows alternate time direction
- * (snake order) so that the width stays h.
+ * (snake order) so that the width stays h. For odd d the odd rows wait in
+ * h - 1 layers only (Proposition 1, odd case): a forward row's last step sums
+ * it out and leaves the top address bit 0, and the next row's first step
+ * creates its value of layer d-1 there; both are steps of the same form.
  *
  * Circuit convention: qubits q = 0..n-1, CZ layers l = 0..d-1, layer l acts
  * on (i, i+1) for every i = l (mod 2) with i+1 < n (Sec. 2.1); one-qubit
@@ -42,8 +45,8 @@ extern "C" {
 enum tb_status {
     TB_OK = 0,
     TB_EINVAL = 1,   /* NULL pointer, bit not in {0,1}, Clifford index > 23, bad size */
-    TB_EDOMAIN = 2,  /* circuit outside what this build contracts: n < 2, d odd or
-                        < 2, ceil(d/2) > 40 for a plan, > 33 for evaluation */
+    TB_EDOMAIN = 2,  /* circuit outside what this build contracts: n < 2, d < 2,
+                        ceil(d/2) > 40 for a plan, > 33 for evaluation */
     TB_ENOMEM = 3,   /* workspace smaller than tb_workspace_bytes() or host allocation failed */
     TB_ECUDA = 4,    /* a CUDA runtime call failed; tb_last_error() has the message */
     TB_ETIMEOUT = 5  /* reserved for bounded device waits */
@@ -112,7 +115,8 @@ typedef struct {
 } tb_plan_info_t;
 
 /* Create a plan (host only: no CUDA call is made).
- *   n, d   : qubits and CZ layers; n >= 2, d even, 2 <= d, ceil(d/2) <= 40
+ *   n, d   : qubits and CZ layers; n >= 2, 2 <= d, ceil(d/2) <= 40 (odd or
+ *            even d)
  *            (else TB_EDOMAIN). Plans wider than 33 bits (2^33 complex64 =
  *            64 GiB) only report their counters: evaluating them returns
  *            TB_EDOMAIN and tb_workspace_bytes returns -1.

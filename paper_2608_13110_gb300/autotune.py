@@ -154,6 +154,6 @@ def tune(h: int, nb: int = 1, n_rows: int = 8, limit: int = 0, use_cache: bool =
 
 def tuned_plan(circ, nb: int | None = None, **kw) -> Plan:
     """Plan for a circuit with autotuned window options."""
-    h = circ.d // 2
+    h = (circ.d + 1) // 2
     opts = tune(h, nb if nb is not None else max(1, circ.bits.shape[0]), **kw)
     return Plan.from_circuit(circ, **opts)

@@ -74,8 +74,11 @@ int open_tables(Plan& P, std::string& err) {
             if (q % 2 == t % 2) js.push_back(q - q0);
     };
     const int l1 = c + ((c % 2) == par ? 0 : 1);  // first late crossing layer
-    const int nlate = h - k;                       // late crossings l1, l1+2, ...
-    if (l1 + 2 * (nlate - 1) > d - 1) {
+    // late crossings l1, l1+2, ..., d-1 or d-2: h - k of them, h - k - 1 when
+    // d is odd and the crossing layers are odd (the boundary's top bit is 0
+    // there and stays as the high half of the last buffer, never read)
+    const int nlate = (d - 1 - l1) / 2 + 1;
+    if (nlate < 1 || nlate > h - k || l1 + 2 * (nlate - 1) > d - 1) {
         err = "internal: late crossings beyond the last layer";
         return TB_EINVAL;
     }

@@ -19,7 +19,8 @@
 //   * prod over coupled pairs of (-1)^(s_(i,l) s_(i+1,l)).
 // Qubit q waits for its partner q+1 in the layers L_q = {l : l = q mod 2}.
 // The boundary after row q is indexed by (s_(q,l)), l in L_q, stored at
-// address bit floor(l/2). For even d every row has h = d/2 such bits.
+// address bit floor(l/2), h = ceil(d/2) bits. For even d every row has h such
+// layers; for odd d the odd rows have h - 1 and their top bit stays 0.
 // Absorbing row r walks its layers in time order (forward for odd r,
 // backward for even r, the snake of Algorithm 1); each step consumes the
 // stored bit of one layer (CZ sign with the row's value, summed) and creates
@@ -29,6 +30,13 @@
 // where c is the value created by the previous step (address bit p-1 forward,
 // p+1 backward). The end steps replace the missing neighbour by the input
 // column U_(r,0)[.,0] or the output row U_(r,d)[x_r,.].
+// Odd d (Proposition 1's turn case): a forward row's last stored layer d-1
+// has no later layer of its own in L_r, so its last step sums the row out,
+//   G[c][0][s] = sum_a U_(r,d)[x_r,a] (-1)^(s a) U_(r,d-1)[a,c], G[c][1][s] = 0,
+// and a backward row starts with nothing to consume: its first step creates
+// the value of layer d-1 from the empty top bit, G[c][a'][0] = U_(r,d)[x_r,a'],
+// G[c][a'][1] = 0. Both keep the form of a controlled 2x2 step, so every
+// kernel runs them unchanged.
 
 #include <algorithm>
 #include <array>
@@ -280,14 +288,15 @@ static void sym_alg1(int n, int d, int* width, double* log2cost) {
 
 int plan_build(Plan& P, int n, int d, const uint8_t* cliff, const uint8_t* tmask,
                const tb_gate1q* extra, int n_extra, const tb_opts* opts, std::string& err) {
-    if (n < 2 || d < 2 || (d % 2) != 0 || (d + 1) / 2 > MAX_PLAN_H) {
-        err = "the planner needs n >= 2, even d >= 2 and ceil(d/2) <= 40";
+    if (n < 2 || d < 2 || (d + 1) / 2 > MAX_PLAN_H) {
+        err = "the planner needs n >= 2, d >= 2 and ceil(d/2) <= 40";
         return TB_EDOMAIN;
     }
     if (n_extra < 0 || (n_extra > 0 && !extra)) { err = "bad extra gate list"; return TB_EINVAL; }
     P.n = n;
     P.d = d;
-    P.h = d / 2;
+    P.h = (d + 1) / 2;
+    const bool odd_d = (d % 2) != 0;
     if (opts) P.opts = *opts;
     else std::memset(&P.opts, 0, sizeof(P.opts));
     const int h = P.h;
@@ -335,6 +344,17 @@ int plan_build(Plan& P, int n, int d, const uint8_t* cliff, const uint8_t* tmask
                     for (int ap = 0; ap < 2; ++ap)
                         for (int s = 0; s < 2; ++s) {
                             cd acc = 0;
+                            if (odd_d && p == h - 1) {  // sum-out (forward) / create (backward)
+                                if (fwd && ap == 0)
+                                    for (int a = 0; a < 2; ++a)
+                                        acc += U(r, d).a[x * 2 + a] * ((s & a) ? -1.0 : 1.0) *
+                                               ((p == 0) ? U(r, 0).a[a * 2 + 0] : U(r, 2 * p).a[a * 2 + c]);
+                                if (!fwd && s == 0)
+                                    acc = U(r, d).a[x * 2 + ap] * ((p == 0) ? U(r, 0).a[ap * 2 + 0] : cd(1.0));
+                                sg.g[x][c * 4 + ap * 2 + s] = f2(acc);
+                                sg64[x * 8 + c * 4 + ap * 2 + s] = acc;
+                                continue;
+                            }
                             for (int a = 0; a < 2; ++a) {
                                 const double sg_ = (s & a) ? -1.0 : 1.0;
                                 cd left, right;
@@ -371,7 +391,9 @@ int plan_build(Plan& P, int n, int d, const uint8_t* cliff, const uint8_t* tmask
     const int k = P.k, m = P.m, top = P.top;
     std::vector<M2> Mp(h);
     for (int p = 1; p < h; ++p) Mp[p] = m2_mul(U(0, 2 * p), U(0, 2 * p - 1));
-    const M2 Eend = m2_mul(U(0, d), U(0, d - 1));
+    // qubit 0 idles in odd layers: after its last stored layer come slots
+    // d-1 and d (even d) or slot d alone (odd d)
+    const M2 Eend = odd_d ? U(0, d) : m2_mul(U(0, d), U(0, d - 1));
     P.init_low.assign((size_t)1 << k, make_float2(0, 0));
     for (int64_t s = 0; s < ((int64_t)1 << k); ++s) {
         cd v = U(0, 0).a[(s & 1) * 2 + 0];
@@ -407,7 +429,9 @@ int plan_build(Plan& P, int n, int d, const uint8_t* cliff, const uint8_t* tmask
 
     // ---- last-row tables: V[s] = e_x^T A_(h-1)(s_(h-1)) ... A_0(s_0) U_(r,0) e_0,
     //      A_p(s) = U_(r,2p+2) D_(2p+1) U_(r,2p+1) D_(2p), D_l = diag(1, (-1)^s)
-    //      on the layers where row r = n-1 meets row n-2.
+    //      on the layers where row r = n-1 meets row n-2. For odd d the last
+    //      factor has no layer d and no slot d+1: A_(h-1)(s) = U_(r,d) D_(d-1)
+    //      (and 0 for s = 1 when layer d-1 is not in L_(n-2): that bit is 0).
     {
         const int r = n - 1;
         auto A = [&](int p, int sbit) {
@@ -416,6 +440,10 @@ int plan_build(Plan& P, int n, int d, const uint8_t* cliff, const uint8_t* tmask
             const bool even_coupled = ((n - 2) % 2) == 0;  // L_(n-2) holds even layers
             const M2 D0 = even_coupled ? D : I2;             // layer 2p
             const M2 D1 = even_coupled ? I2 : D;             // layer 2p+1
+            if (odd_d && p == h - 1) {
+                if (!even_coupled && sbit) return m2(0, 0, 0, 0);
+                return m2_mul(U(r, d), D0);
+            }
             return m2_mul(U(r, 2 * p + 2), m2_mul(D1, m2_mul(U(r, 2 * p + 1), D0)));
         };
         std::vector<std::array<M2, 2>> Acache(h);

@@ -53,6 +53,10 @@ def test_constructive_width_is_ceil_d_over_2(tb):
     for n, d in [(12, 8), (30, 40), (32, 48), (70, 56), (70, 64), (20, 16), (40, 48)]:
         info = tb.Plan(n, d).info
         assert info["width"] == d // 2 == info["boundary_bits"]
+    # odd d (Proposition 1's turn case): the same width ceil(d/2)
+    for n, d in [(4, 7), (12, 9), (30, 41), (70, 7), (70, 63), (70, 65), (40, 79), (9, 17)]:
+        info = tb.Plan(n, d).info
+        assert info["width"] == (d + 1) // 2 == info["boundary_bits"], (n, d)
 
 
 def test_boundary_payload_bytes(tb):
@@ -81,9 +85,9 @@ def test_plan_topology_independent_of_gate_values(tb):
 
 
 def test_step_and_pass_counts(tb):
-    for n, d in [(70, 64), (70, 56), (30, 40), (12, 8), (2, 30), (3, 26)]:
+    for n, d in [(70, 64), (70, 56), (30, 40), (12, 8), (2, 30), (3, 26), (70, 63), (13, 25), (5, 9)]:
         info = tb.Plan(n, d).info
-        h = d // 2
+        h = (d + 1) // 2
         assert info["n_steps"] == max(0, n - 2) * h
         if h <= 12 or n == 2:
             assert info["n_passes"] == 0
@@ -104,7 +108,7 @@ def test_window_options(tb):
         tb.Plan(40, 60, window_bits=4)
 
 
-@pytest.mark.parametrize("n,d", [(1, 8), (10, 7), (10, 0), (10, 82), (0, 4)])
+@pytest.mark.parametrize("n,d", [(1, 8), (10, 1), (10, 0), (10, 82), (10, 81), (0, 4)])
 def test_domain_errors(tb, n, d):
     with pytest.raises(tb.TbError) as e:
         tb.Plan(n, d)
