@@ -138,13 +138,20 @@ def _cpu_model() -> str:
     return f"{platform.machine()} ({os.cpu_count()} logical CPUs)"
 
 
-def cpu_baseline(seconds_cap: float = 30.0) -> dict:
+def cpu_sample_circuit():
+    return W.random_circuit(CPU_SAMPLE[0], CPU_SAMPLE[1], None, 4, 777)
+
+
+def cpu_baseline(seconds_cap: float = 30.0, threads: int = 0) -> dict:
     """FP64 oracle (naive row-by-row contraction) on the n=30, d=40 slice with
     the workload's gate statistics, scaled to the n=70, d=64 workload by the
-    ratio of Algorithm 1's contraction costs of the two circuits."""
+    ratio of Algorithm 1's contraction costs of the two circuits. threads > 0
+    limits the oracle's OpenMP threads (all host cores otherwise)."""
     import oracle
     import paper_2608_13110_gb300 as tb
-    c = W.random_circuit(CPU_SAMPLE[0], CPU_SAMPLE[1], None, 4, 777)
+    if threads > 0:
+        oracle.set_num_threads(threads)
+    c = cpu_sample_circuit()
     u = oracle.circuit_gates(c)
     done = 0
     t0 = time.perf_counter()
@@ -157,7 +164,7 @@ def cpu_baseline(seconds_cap: float = 30.0) -> dict:
     slice_rate = done / dt
     ratio = 2.0 ** (tb.Plan(70, 64).info["log2_cost"] - tb.Plan(*CPU_SAMPLE).info["log2_cost"])
     return {"value": slice_rate / ratio, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "cpu": _cpu_model(),
+            "cpu": _cpu_model(), "sample_amps_per_s": slice_rate,
             "sample": (f"{done} amplitude(s) of an n={CPU_SAMPLE[0]}, d={CPU_SAMPLE[1]} slice (width 20) "
                        f"in {dt:.1f} s = {slice_rate:.3g} amps/s, divided by the Algorithm 1 cost ratio "
                        f"C(70,64)/C(30,40) = {ratio:.4g}")}
@@ -193,8 +200,8 @@ def run_reference(args, rank, world):
     steps, warm = args.steps, args.warmup
     per_step = max(2.0, min(20.0, 150.0 / max(1, steps + warm)))
     for _ in range(warm):
-        cpu_baseline(per_step)
-    vals = [cpu_baseline(per_step) for _ in range(steps)]
+        cpu_baseline(per_step, args.cpu_threads)
+    vals = [cpu_baseline(per_step, args.cpu_threads) for _ in range(steps)]
     v = statistics.median(x["value"] for x in vals)
     cb = dict(vals[-1])
     cb["value"] = v
@@ -316,9 +323,44 @@ def run_ours(args, rank, world, local):
         "sanity": {"log_xeb": tb.log_xeb(amps, 70), "e2e_matches_device": bool(np.array_equal(amps, e2e_amps))},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, args.cpu_threads)
+        line["cpu_baseline"]["gpu_same_sample"] = gpu_rate_on_cpu_sample(tb, dev, stream, line["cpu_baseline"])
     if rank == 0:
         print(json.dumps(line))
+
+
+def gpu_rate_on_cpu_sample(tb, dev, stream, cb):
+    """The device path on the oracle's own sample (the same n=30, d=40 circuit
+    and bitstrings, each repeated 64 times per call): a like-for-like amps/s
+    beside the oracle's unscaled slice rate."""
+    import torch
+    c = cpu_sample_circuit()
+    bits = np.repeat(c.bits, 64, axis=0)
+    plan = tb.Plan.from_circuit(c)
+    ws = torch.empty(plan.workspace_bytes(bits.shape[0]), dtype=torch.uint8, device=dev)
+    plan.upload(ws, stream)
+    d_bits = torch.from_numpy(bits).to(dev)
+    d_out = torch.empty((bits.shape[0], 2), dtype=torch.float64, device=dev)
+    for _ in range(3):
+        plan.amplitudes_device(d_bits, ws, d_out, stream)
+    reps = 5
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(reps):
+        plan.amplitudes_device(d_bits, ws, d_out, stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    rate = reps * bits.shape[0] / (e0.elapsed_time(e1) / 1e3)
+    got = d_out.cpu().numpy().view(np.complex128).reshape(-1)
+    oracle_rate = cb.get("sample_amps_per_s")
+    return {"value": rate, "unit": "amps/s on the sample circuit",
+            "ratio_to_oracle_sample_rate": (rate / oracle_rate) if oracle_rate else None,
+            "repeats_identical": bool(np.all(got.reshape(4, 64) == got.reshape(4, 64)[:, :1])),
+            "how": f"{bits.shape[0]} bitstrings per call ({c.bits.shape[0]} distinct x 64), "
+                   f"{reps} calls after 3 warm-up calls, CUDA events on the launching stream; the "
+                   f"8 MiB boundaries fit L2, unlike the n=70, d=64 workload"}
 
 
 def run_batch_workload(args, rank, world, local):
@@ -666,6 +708,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-threads", type=int, default=0,
+                    help="OpenMP threads of the CPU oracle baseline (0 = every host core)")
     ap.add_argument("--workload", default="n70d64", choices=("n70d64", "batch", "serve", "precision", "open"),
                     help="n70d64: the headline metric; batch: 64 uneven circuits in one graph; "
                          "serve: Poisson request stream through the serving runtime; "

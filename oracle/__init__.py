@@ -70,8 +70,9 @@ def _load():
         lib.tbo_feynman.argtypes = [ctypes.c_int, ctypes.c_int, dp, u8p, dp]
         lib.tbo_tableau_prob.argtypes = [ctypes.c_int, ctypes.c_int, u8p, u8p, dp]
         lib.tbo_num_threads.argtypes = []
+        lib.tbo_set_num_threads.argtypes = [ctypes.c_int]
         for f in ("tbo_sv_state", "tbo_nb_amplitude", "tbo_feynman", "tbo_tableau_prob",
-                  "tbo_num_threads"):
+                  "tbo_num_threads", "tbo_set_num_threads"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -80,6 +81,11 @@ def _load():
 def num_threads() -> int:
     """OpenMP threads the C oracle uses."""
     return int(_load().tbo_num_threads())
+
+
+def set_num_threads(t: int) -> int:
+    """Use t OpenMP threads from now on (t >= 1); returns the count in effect."""
+    return int(_load().tbo_set_num_threads(int(t)))
 
 
 def _dptr(a: np.ndarray):

@@ -53,6 +53,17 @@ int tbo_num_threads(void) {
 #endif
 }
 
+/* Set the OpenMP thread count of later calls (t >= 1); returns the count. */
+int tbo_set_num_threads(int t) {
+#ifdef _OPENMP
+    if (t >= 1) omp_set_num_threads(t);
+    return omp_get_max_threads();
+#else
+    (void)t;
+    return 1;
+#endif
+}
+
 /* ------------------------------------------------------------------------ */
 /* Dense state vector. out: 2*2^n doubles (re, im), index bit q = qubit q.   */
 /* ------------------------------------------------------------------------ */
