@@ -137,6 +137,22 @@ def test_closed_form_70_64(tb, oracle_mod):
     assert rel_l2(got, ref) < TOL
 
 
+def test_closed_form_70_64_tuned_schedule_batch_16(tb, oracle_mod):
+    """The benchmark's launch configuration at full size: n=70, d=64, 16
+    bitstrings evaluated side by side, windows of 9 bits, bottom 10, top 7 (the
+    schedule the autotuner picks for width 32 on a GB300), against the closed
+    form of an H / diagonal / H circuit."""
+    c = W.hdiag_circuit(70, 64, 426, 0, 4100)
+    bits = _nonzero_bits(c, oracle_mod, 16, 7)
+    plan = tb.Plan.from_circuit(c, window_bits=9, bottom_bits=10, top_bits=7)
+    assert plan.info["n_passes"] == 205
+    ref = oracle_mod.closed_form_hdiag(c, bits)
+    got = plan.amplitudes(bits)
+    assert rel_l2(got, ref) < TOL
+    # each amplitude on its own scale too (the closed form varies over decades)
+    assert np.max(np.abs(got - ref) / np.abs(ref)) < 1e-4
+
+
 def test_closed_form_70_62(tb, oracle_mod):
     """d = 2 (mod 4): every edge keeps an odd number of CZ layers, so the
     amplitude is a chain sum, not a product."""
