@@ -318,7 +318,8 @@ def run_ours(args, rank, world, local):
                      "kernel": "pass_kernel" if args.precision == "fp32" else "tc_pass_kernel",
                      "peak_source": f"{peak_src} copy bandwidth",
                      "pass_launches": p["launches"], "pass_ms_total": p["ms"],
-                     "pass_share_of_kernel_time": p["ms"] / max(1e-9, sum(v["ms"] for v in prof.values()))},
+                     "pass_share_of_kernel_time": p["ms"] / max(1e-9, sum(v["ms"] for v in prof.values())),
+                     "fma_pipe": fma_pipe_fraction(args, info, nb, h, p, clk, dev)},
         "clocks": clk,
         "sanity": {"log_xeb": tb.log_xeb(amps, 70), "e2e_matches_device": bool(np.array_equal(amps, e2e_amps))},
     }
@@ -327,6 +328,24 @@ def run_ours(args, rank, world, local):
         line["cpu_baseline"]["gpu_same_sample"] = gpu_rate_on_cpu_sample(tb, dev, stream, line["cpu_baseline"])
     if rank == 0:
         print(json.dumps(line))
+
+
+def fma_pipe_fraction(args, info, nb, h, p, clk, dev):
+    """The FP32 passes' other ceiling: 8 FMA per entry per paired step, over
+    the pass kernels' measured time, against SMs x 128 FP32 lanes x the SM
+    clock (one FMA per lane and cycle; the paired FFMA2 issues two lanes' worth
+    in two cycles). Secondary to the HBM roofline: the two floors are within
+    15 % of each other at width 32."""
+    if args.precision != "fp32" or p["ms"] <= 0:
+        return None
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clk.get("sm_max_mhz") or 2070.0
+    fma = 8.0 * nb * args.steps * info["n_steps"] * 2.0 ** h
+    achieved = fma / (p["ms"] / 1e3) / 1e12
+    peak = sms * 128 * mhz * 1e6 / 1e12
+    return {"achieved": achieved, "peak": peak, "unit": "TFMA/s", "frac": achieved / peak,
+            "peak_source": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz"}
 
 
 def gpu_rate_on_cpu_sample(tb, dev, stream, cb):
