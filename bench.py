@@ -378,8 +378,8 @@ def gpu_rate_on_cpu_sample(tb, dev, stream, cb):
             "ratio_to_oracle_sample_rate": (rate / oracle_rate) if oracle_rate else None,
             "repeats_identical": bool(np.all(got.reshape(4, 64) == got.reshape(4, 64)[:, :1])),
             "how": f"{bits.shape[0]} bitstrings per call ({c.bits.shape[0]} distinct x 64), "
-                   f"{reps} calls after 3 warm-up calls, CUDA events on the launching stream; the "
-                   f"8 MiB boundaries fit L2, unlike the n=70, d=64 workload"}
+                   f"{reps} calls after 3 warm-up calls, CUDA events on the launching stream; "
+                   f"256 boundaries of 8 MiB in flight (2 GiB, larger than L2), planner-default windows"}
 
 
 def run_batch_workload(args, rank, world, local):
