@@ -65,7 +65,7 @@ def _load():
         dp = ctypes.POINTER(ctypes.c_double)
         u8p = ctypes.POINTER(ctypes.c_uint8)
         ip = ctypes.POINTER(ctypes.c_int)
-        lib.tbo_sv_state.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp]
+        lib.tbo_sv_state.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_void_p, dp]
         lib.tbo_nb_amplitude.argtypes = [ctypes.c_int, ctypes.c_int, dp, u8p, dp, ip]
         lib.tbo_feynman.argtypes = [ctypes.c_int, ctypes.c_int, dp, u8p, dp]
         lib.tbo_tableau_prob.argtypes = [ctypes.c_int, ctypes.c_int, u8p, u8p, dp]
@@ -148,13 +148,25 @@ def _flat(u: np.ndarray) -> np.ndarray:
 # Amplitudes
 # --------------------------------------------------------------------------
 
-def sv_state(n: int, d: int, u: np.ndarray) -> np.ndarray:
-    """Full state U|0^n> (2^n complex128, basis index bit q = x_q)."""
+def _phases(n: int, d: int, phase):
+    """None, or the (d, n-1) controlled-phase angles as a flat C array."""
+    if phase is None:
+        return None
+    ph = np.ascontiguousarray(np.asarray(phase, np.float64).reshape(d, n - 1))
+    return ph
+
+
+def sv_state(n: int, d: int, u: np.ndarray, phase=None) -> np.ndarray:
+    """Full state U|0^n> (2^n complex128, basis index bit q = x_q). phase:
+    None (CZ entanglers) or (d, n-1) angles, phase[l, i] the controlled phase
+    diag(1, 1, 1, e^(i phase)) on (i, i+1) in layer l (entries of uncoupled
+    pairs are ignored)."""
     lib = _load()
     fu = _flat(u)
     assert fu.size == (d + 1) * n * 8
+    ph = _phases(n, d, phase)
     out = np.empty(2 << n, np.float64)
-    rc = lib.tbo_sv_state(n, d, _dptr(fu), _dptr(out))
+    rc = lib.tbo_sv_state(n, d, _dptr(fu), None if ph is None else ph.ctypes.data, _dptr(out))
     if rc:
         raise RuntimeError(f"tbo_sv_state failed ({rc})")
     return out.view(np.complex128)
@@ -165,8 +177,8 @@ def basis_index(bits: np.ndarray) -> np.ndarray:
     return (bits << np.arange(bits.shape[1], dtype=np.int64)).sum(axis=1)
 
 
-def sv_amplitudes(n: int, d: int, u: np.ndarray, bits: np.ndarray) -> np.ndarray:
-    return sv_state(n, d, u)[basis_index(bits)]
+def sv_amplitudes(n: int, d: int, u: np.ndarray, bits: np.ndarray, phase=None) -> np.ndarray:
+    return sv_state(n, d, u, phase)[basis_index(bits)]
 
 
 def nb_amplitudes(n: int, d: int, u: np.ndarray, bits: np.ndarray,
@@ -202,12 +214,15 @@ def feynman_amplitude(n: int, d: int, u: np.ndarray, x) -> complex:
     return complex(o[0], o[1])
 
 
-def kron_state(n: int, d: int, u: np.ndarray) -> np.ndarray:
+def kron_state(n: int, d: int, u: np.ndarray, phase=None) -> np.ndarray:
     """U|0^n> from explicit 2^n x 2^n matrices: each slot is the Kronecker
-    product of its one-qubit gates, each CZ layer a diagonal +-1 matrix built
-    from the coupled pairs. Basis index bit q = qubit q, so qubit n-1 is the
-    leftmost Kronecker factor."""
+    product of its one-qubit gates, each entangling layer the product of its
+    two-qubit gates, each the 4x4 diag(1, 1, 1, w) (w = -1 for CZ, e^(i phase)
+    otherwise) embedded by Kronecker products with identities. Basis index bit
+    q = qubit q, so qubit n-1 is the leftmost Kronecker factor."""
     u = np.asarray(u, np.complex128)
+    if phase is not None:
+        phase = np.asarray(phase, np.float64).reshape(d, n - 1)
     dim = 1 << n
     idx = np.arange(dim)
     state = np.zeros(dim, np.complex128)
@@ -218,11 +233,13 @@ def kron_state(n: int, d: int, u: np.ndarray) -> np.ndarray:
             m = np.kron(m, u[t, q])
         state = m @ state
         if t < d:
-            diag = np.ones(dim)
+            layer = np.eye(dim, dtype=np.complex128)
             for i0 in range(t % 2, n - 1, 2):
-                both = ((idx >> i0) & 1) & ((idx >> (i0 + 1)) & 1)
-                diag = diag * np.where(both == 1, -1.0, 1.0)
-            state = diag * state
+                w = -1.0 if phase is None else np.exp(1j * phase[t, i0])
+                g = np.diag([1.0, 1.0, 1.0, w]).astype(np.complex128)  # basis (q_(i0+1), q_i0)
+                full = np.kron(np.kron(np.eye(1 << (n - i0 - 2)), g), np.eye(1 << i0))
+                layer = full @ layer
+            state = layer @ state
     return state
 
 
@@ -240,15 +257,16 @@ def tableau_probability(circ, x) -> float:
     return float(p.value)
 
 
-def closed_form_hdiag(circ, bits: np.ndarray) -> np.ndarray:
+def closed_form_hdiag(circ, bits: np.ndarray, phase=None) -> np.ndarray:
     """Exact amplitudes of an H / diagonal / H circuit.
 
     With H on every qubit at slot 0 and slot d and only diagonal gates in
     between (Cliffords I, Z, S, Z.S and T), everything between the two H layers
-    commutes and multiplies |y> by exp(i theta.y) (-1)^(sum_e m_e y_i y_(i+1)),
-    where theta_q collects the diagonal phases of qubit q and m_e is the parity
-    of the number of CZ layers on edge e. Hence
-        psi(x) = 2^-n sum_y exp(i theta.y) (-1)^(sum_e m_e y_i y_(i+1) + x.y),
+    commutes and multiplies |y> by exp(i theta.y) exp(i sum_e Phi_e y_i y_(i+1)),
+    where theta_q collects the diagonal phases of qubit q and Phi_e the angles
+    of the entangling gates on edge e (pi per CZ, so Phi_e = pi m_e with m_e the
+    number of its CZ layers; phase[l, i] per gate otherwise). Hence
+        psi(x) = 2^-n sum_y exp(i theta.y) exp(i sum_e Phi_e y_i y_(i+1)) (-1)^(x.y),
     evaluated with a 2x2 transfer matrix along the chain."""
     n, d = circ.n, circ.d
     tab = clifford_table()
@@ -263,15 +281,20 @@ def closed_form_hdiag(circ, bits: np.ndarray) -> np.ndarray:
                 raise ValueError("interior slots must be diagonal with (0,0) entry 1")
             theta[q] += np.angle(c[1, 1])
     theta += (np.pi / 4) * circ.tmask.sum(axis=0)
-    m = np.array([sum(1 for l in range(d) if l % 2 == i % 2) % 2 for i in range(n - 1)])
+    if phase is None:
+        m = np.array([sum(1 for l in range(d) if l % 2 == i % 2) % 2 for i in range(n - 1)])
+        w_edge = np.where(m == 1, -1.0, 1.0).astype(np.complex128)
+    else:
+        phase = np.asarray(phase, np.float64).reshape(d, n - 1)
+        big_phi = np.array([sum(phase[l, i] for l in range(d) if l % 2 == i % 2) for i in range(n - 1)])
+        w_edge = np.exp(1j * big_phi)
     bits = np.atleast_2d(bits)
     out = np.empty(bits.shape[0], np.complex128)
     for b, x in enumerate(bits):
         ph = np.exp(1j * theta) * np.where(x == 1, -1.0, 1.0)
         v = np.array([1.0 + 0j, ph[0]])
         for q in range(1, n):
-            s = -1.0 if m[q - 1] else 1.0
-            v = np.array([v[0] + v[1], (v[0] + s * v[1]) * ph[q]])
+            v = np.array([v[0] + v[1], (v[0] + w_edge[q - 1] * v[1]) * ph[q]])
         out[b] = (v[0] + v[1]) / (2.0 ** n)
     return out
 

@@ -20,7 +20,10 @@
  *   - bitstring x: x[q] in {0,1}; state-vector basis index bit q = x_q.
  *
  * Contents:
- *   tbo_sv_state      dense state vector (the definition written out)
+ *   tbo_sv_state      dense state vector (the definition written out); its
+ *                     entangler may also be a controlled phase diag(1,1,1,
+ *                     e^(i phi)) per gate (phi = pi is CZ; Sec. 2.1 allows any
+ *                     two-qubit gate of operator Schmidt rank 2)
  *   tbo_nb_amplitude  naive boundary contraction over qubit rows, every row
  *                     in forward time with an explicit wire index (the
  *                     network of Sec. 2.2 contracted row by row; no slot
@@ -66,8 +69,10 @@ int tbo_set_num_threads(int t) {
 
 /* ------------------------------------------------------------------------ */
 /* Dense state vector. out: 2*2^n doubles (re, im), index bit q = qubit q.   */
+/* ph: NULL (every entangler is CZ) or d*(n-1) phases, ph[l*(n-1) + i] the   */
+/* angle of the controlled-phase gate on (i, i+1) in layer l.                */
 /* ------------------------------------------------------------------------ */
-int tbo_sv_state(int n, int d, const double* u, double* out) {
+int tbo_sv_state(int n, int d, const double* u, const double* ph, double* out) {
     if (n < 1 || n > 30 || d < 0) return -1;
     const int64_t N = (int64_t)1 << n;
     cplx* psi = (cplx*)calloc((size_t)N, sizeof(cplx));
@@ -87,12 +92,14 @@ int tbo_sv_state(int n, int d, const double* u, double* out) {
             }
         }
         if (t == d) break;
-        /* CZ layer t: phase -1 when both qubits of a coupled pair are 1. */
+        /* entangling layer t: phase -1 (CZ) or e^(i phi) when both qubits of a
+           coupled pair are 1. */
         for (int i0 = t % 2; i0 + 1 < n; i0 += 2) {
             const int64_t m = ((int64_t)1 << i0) | ((int64_t)1 << (i0 + 1));
+            const cplx w = ph ? cexp(I * ph[(size_t)t * (n - 1) + i0]) : -1.0;
 #pragma omp parallel for schedule(static)
             for (int64_t i = 0; i < N; ++i)
-                if ((i & m) == m) psi[i] = -psi[i];
+                if ((i & m) == m) psi[i] = ph ? w * psi[i] : -psi[i];
         }
     }
     for (int64_t i = 0; i < N; ++i) {

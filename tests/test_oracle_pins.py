@@ -7,6 +7,10 @@ Each check is chosen so that a plausible mistake fails it:
   * a dropped or doubled term in the row contraction -> brute force, norm = 1
   * a wrong Clifford decomposition in the tableau -> tableau vs Kronecker product
   * a wrong T phase or T/Clifford order   -> explicit matrix checks, closed form
+  * a controlled phase on the wrong pair or layer, or a conjugated one
+                                          -> worked example, Kronecker product with
+                                             random angles, phi = pi (CZ) and phi = 0
+                                             (product state), closed form
 """
 import itertools
 
@@ -201,6 +205,56 @@ def test_identity_circuit(oracle_mod):
         u = oracle_mod.circuit_gates(c)
         exp = np.array([1.0 if not x.any() else 0.0 for x in c.bits])
         np.testing.assert_allclose(oracle_mod.nb_amplitudes(n, d, u, c.bits), exp, atol=1e-15)
+
+
+# ------------------------------------------------ controlled-phase entanglers
+
+def test_controlled_phase_worked_example(oracle_mod):
+    """H on both qubits, then diag(1, 1, 1, e^(i phi)): the state is
+    (|00> + |01> + |10> + e^(i phi)|11>) / 2."""
+    phi = 0.7
+    u = np.tile(np.eye(2, dtype=np.complex128), (2, 2, 1, 1))
+    u[0, :] = np.array([[1, 1], [1, -1]]) / np.sqrt(2.0)
+    exp = np.array([1, 1, 1, np.exp(1j * phi)]) / 2.0
+    ph = np.array([[phi]])
+    np.testing.assert_allclose(oracle_mod.sv_state(2, 1, u, ph), exp, atol=1e-15)
+    np.testing.assert_allclose(oracle_mod.kron_state(2, 1, u, ph), exp, atol=1e-15)
+
+
+@pytest.mark.parametrize("n,d", [(2, 3), (3, 4), (4, 5), (5, 6), (6, 3), (7, 4)])
+def test_controlled_phase_sv_matches_kronecker_product(oracle_mod, n, d):
+    u = W.random_unitaries(n, d, 300 + n + d)
+    ph = W.random_phases(n, d, 400 + n + d)
+    np.testing.assert_allclose(oracle_mod.sv_state(n, d, u, ph), oracle_mod.kron_state(n, d, u, ph),
+                               atol=1e-13)
+
+
+def test_controlled_phase_pi_is_cz_and_zero_is_a_product(oracle_mod):
+    n, d = 6, 7
+    u = W.random_unitaries(n, d, 77)
+    np.testing.assert_allclose(oracle_mod.sv_state(n, d, u, np.full((d, n - 1), np.pi)),
+                               oracle_mod.sv_state(n, d, u), atol=1e-14)
+    # no entanglement: the state is the Kronecker product of each qubit's chain
+    psi = oracle_mod.sv_state(n, d, u, np.zeros((d, n - 1)))
+    cols = []
+    for q in range(n):
+        v = np.array([1.0, 0.0], np.complex128)
+        for t in range(d + 1):
+            v = u[t, q] @ v
+        cols.append(v)
+    prod = np.ones(1, np.complex128)
+    for q in reversed(range(n)):
+        prod = np.kron(prod, cols[q])
+    np.testing.assert_allclose(psi, prod, atol=1e-14)
+
+
+@pytest.mark.parametrize("n,d", [(6, 4), (7, 7), (8, 9), (9, 6)])
+def test_controlled_phase_closed_form_matches_state_vector(oracle_mod, n, d):
+    c = W.hdiag_circuit(n, d, 3 * n, 0, 60 + n + d)
+    ph = W.random_phases(n, d, 70 + n + d)
+    bits = _all_bits(n)
+    ref = oracle_mod.sv_amplitudes(n, d, oracle_mod.circuit_gates(c), bits, ph)
+    np.testing.assert_allclose(oracle_mod.closed_form_hdiag(c, bits, ph), ref, atol=1e-13)
 
 
 # ---------------------------------------------------------------- log-XEB

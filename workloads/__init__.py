@@ -117,6 +117,13 @@ def random_unitaries(n: int, d: int, seed: int) -> np.ndarray:
     return q * ph[..., None, :]
 
 
+def random_phases(n: int, d: int, seed: int) -> np.ndarray:
+    """(d, n-1) angles uniform in [0, 2 pi): one controlled-phase angle per
+    (layer, pair); entries of pairs a layer does not couple are drawn too and
+    ignored by both sides."""
+    return np.random.default_rng(seed).uniform(0.0, 2.0 * np.pi, size=(d, max(n - 1, 0)))
+
+
 # --- The five workload shapes (seed = config_id*1000 + replica) -------------
 
 def tiny(replica: int = 0) -> Circuit:
