@@ -152,6 +152,24 @@ TB_API int tb_plan_create_open(int n, int d, const uint8_t* cliff, const uint8_t
                                const tb_gate1q* extra, int n_extra, const tb_opts* opts, int k,
                                tb_plan** out);
 
+/* Create a plan whose entanglers are controlled phases. Sec. 2.1 admits any
+ * two-qubit entangler of operator Schmidt rank 2 in the brickwork; the sweep
+ * only ever uses the diagonal factor w^(s s') that such a gate contributes for
+ * the two qubits' values s, s' in its layer (w = -1 is CZ), so each entangler
+ * here is diag(1, 1, 1, e^(i phi)).
+ *   cphase: NULL (every entangler is CZ) or d*(n-1) angles in radians,
+ *           cphase[l*(n-1) + i] for the pair (i, i+1) in layer l; entries of
+ *           pairs a layer does not couple (i != l mod 2) are ignored. A
+ *           non-finite angle of a coupled pair returns TB_EINVAL; phi = pi
+ *           exactly gives the same plan as CZ. The array is copied.
+ *   open_k: 0 for a plain plan (as tb_plan_create), else the open bits of
+ *           tb_plan_create_open with its domain.
+ * Other arguments, evaluation and errors as tb_plan_create. Width and cost
+ * counters do not depend on the angles. */
+TB_API int tb_plan_create_cphase(int n, int d, const uint8_t* cliff, const uint8_t* tmask,
+                                 const tb_gate1q* extra, int n_extra, const double* cphase,
+                                 const tb_opts* opts, int open_k, tb_plan** out);
+
 /* Batched sampling from open-plan amplitudes (Sec. 4, "Batched sampling"):
  * for each of na prefixes with amplitudes amps[a*2^k .. (a+1)*2^k) ((re, im)
  * pairs, host FP64), Q_a = sum_b |amp|^2 and the suffix b drawn from

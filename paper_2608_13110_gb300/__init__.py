@@ -78,6 +78,9 @@ _sig = {
     "tb_plan_create_open": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _u8p, _u8p, ctypes.POINTER(_Gate1q),
                                            ctypes.c_int, ctypes.POINTER(_Opts), ctypes.c_int,
                                            ctypes.POINTER(_vp)]),
+    "tb_plan_create_cphase": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _u8p, _u8p, ctypes.POINTER(_Gate1q),
+                                             ctypes.c_int, _dp, ctypes.POINTER(_Opts), ctypes.c_int,
+                                             ctypes.POINTER(_vp)]),
     "tb_batched_sample": (ctypes.c_int, [_dp, ctypes.c_int, ctypes.c_int64, _dp,
                                          ctypes.POINTER(ctypes.c_int32), _dp]),
 }
@@ -210,11 +213,13 @@ class Plan:
     """A planned circuit: folded gates, step tables and pass schedule.
 
     cliff: (d+1, n) Clifford indices (None = identity); tmask: (d, n) 0/1
-    (None = no T); extra: iterable of (qubit, slot, 2x2 complex matrix)."""
+    (None = no T); extra: iterable of (qubit, slot, 2x2 complex matrix);
+    cphase: None (CZ entanglers) or (d, n-1) angles, cphase[l, i] the
+    controlled phase diag(1, 1, 1, e^(i phi)) on (i, i+1) in layer l."""
 
     def __init__(self, n: int, d: int, cliff=None, tmask=None, extra=None, *,
                  window_bits: int = 0, bottom_bits: int = 0, top_bits: int = 0,
-                 hbm_budget_bytes: int = 0, precision=0, open_k: int = 0):
+                 hbm_budget_bytes: int = 0, precision=0, open_k: int = 0, cphase=None):
         self.n, self.d = int(n), int(d)
         self._cliff = None if cliff is None else _u8(cliff).reshape(-1)
         self._tmask = None if tmask is None else _u8(tmask).reshape(-1)
@@ -236,7 +241,15 @@ class Plan:
         cp = None if self._cliff is None else self._cliff.ctypes.data_as(_u8p)
         tp = None if self._tmask is None else self._tmask.ctypes.data_as(_u8p)
         self.open_k = int(open_k)
-        if self.open_k:
+        if cphase is not None:
+            ph = np.ascontiguousarray(np.asarray(cphase, np.float64).reshape(-1))
+            if ph.size != self.d * max(self.n - 1, 0):
+                raise ValueError("cphase must have d*(n-1) entries")
+            self._cphase = ph
+            _check(_lib.tb_plan_create_cphase(self.n, self.d, cp, tp, arr if ex else None, len(ex),
+                                              ph.ctypes.data_as(_dp), ctypes.byref(opts), self.open_k,
+                                              ctypes.byref(h)), "tb_plan_create_cphase")
+        elif self.open_k:
             _check(_lib.tb_plan_create_open(self.n, self.d, cp, tp, arr if ex else None, len(ex),
                                             ctypes.byref(opts), self.open_k, ctypes.byref(h)),
                    "tb_plan_create_open")

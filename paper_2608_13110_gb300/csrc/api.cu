@@ -284,6 +284,7 @@ int run_device(const Plan& P, const uint8_t* d_bits, int64_t nb, void* d_ws, int
                 lp.k = k;
                 lp.ops = ops + P.open_seg[i];
                 lp.nops = P.open_seg[i + 1] - P.open_seg[i];
+                lp.w = P.open_w[i];
                 const int64_t chunks = ((lp.out_entries + (1 << OPEN_CHUNK_BITS) - 1) >> OPEN_CHUNK_BITS) * nbat;
                 ProfScope ps(PC_LATE, 24.0 * (double)nbat * (double)lp.out_entries, st);
                 TB_CUDA(launch_late(lp, (int)std::min<int64_t>(chunks, 8LL * nsm), st));
@@ -364,39 +365,30 @@ extern "C" {
 
 int tb_plan_create(int n, int d, const uint8_t* cliff, const uint8_t* tmask, const tb_gate1q* extra,
                    int n_extra, const tb_opts* opts, tb_plan** out) {
-    if (!out) return fail(TB_EINVAL, "out is NULL");
-    *out = nullptr;
-    try {
-        tb_plan* p = new tb_plan;
-        std::string err;
-        const int rc = plan_build(p->p, n, d, cliff, tmask, extra, n_extra, opts, err);
-        if (rc != TB_OK) {
-            delete p;
-            return fail(rc, err);
-        }
-        p->p.uid = next_plan_uid();
-        *out = p;
-        return TB_OK;
-    } catch (const std::bad_alloc&) {
-        return fail(TB_ENOMEM, "host allocation failed");
-    } catch (...) {
-        return fail(TB_EINVAL, "plan construction failed");
-    }
+    return tb_plan_create_cphase(n, d, cliff, tmask, extra, n_extra, nullptr, opts, 0, out);
 }
 
 int tb_plan_create_open(int n, int d, const uint8_t* cliff, const uint8_t* tmask, const tb_gate1q* extra,
                         int n_extra, const tb_opts* opts, int k, tb_plan** out) {
+    if (k < 1) return fail(TB_EDOMAIN, "open bits k must satisfy 1 <= k <= min(floor(d/4), 10, n-1)");
+    return tb_plan_create_cphase(n, d, cliff, tmask, extra, n_extra, nullptr, opts, k, out);
+}
+
+int tb_plan_create_cphase(int n, int d, const uint8_t* cliff, const uint8_t* tmask, const tb_gate1q* extra,
+                          int n_extra, const double* cphase, const tb_opts* opts, int open_k, tb_plan** out) {
     if (!out) return fail(TB_EINVAL, "out is NULL");
     *out = nullptr;
-    const int h = (d + 1) / 2;
-    if (k < 1 || k > d / 4 || k > OPEN_MAX_K || k > n - 1)
-        return fail(TB_EDOMAIN, "open bits k must satisfy 1 <= k <= min(floor(d/4), 10, n-1)");
-    if (h <= SMALL_H_MAX) return fail(TB_EDOMAIN, "open plans need ceil(d/2) >= 13");
+    if (open_k != 0) {
+        const int h = (d + 1) / 2;
+        if (open_k < 1 || open_k > d / 4 || open_k > OPEN_MAX_K || open_k > n - 1)
+            return fail(TB_EDOMAIN, "open bits k must satisfy 1 <= k <= min(floor(d/4), 10, n-1)");
+        if (h <= SMALL_H_MAX) return fail(TB_EDOMAIN, "open plans need ceil(d/2) >= 13");
+    }
     try {
         tb_plan* p = new tb_plan;
-        p->p.open_k = k;
+        p->p.open_k = open_k;
         std::string err;
-        const int rc = plan_build(p->p, n, d, cliff, tmask, extra, n_extra, opts, err);
+        const int rc = plan_build(p->p, n, d, cliff, tmask, extra, n_extra, cphase, opts, err);
         if (rc != TB_OK) {
             delete p;
             return fail(rc, err);

@@ -77,7 +77,8 @@ __global__ void __launch_bounds__(256, 2) join_kernel(const JoinParams p) {
     }
 }
 
-// One late crossing: out[r'][y] = seg( in[2r'][y] + (-1)^(y_0) in[2r'+1][y] ).
+// One late crossing: out[r'][y] = seg( in[2r'][y] + w^(y_0) in[2r'+1][y] ),
+// w = -1 for CZ (diag(1, 1, 1, w) in general).
 // A CTA works on chunks of 2^OPEN_CHUNK_BITS output entries (or one row when
 // 2^k is larger) in shared memory; the segment's operations act on chunk
 // index bits 0..k-1.
@@ -105,7 +106,8 @@ __global__ void __launch_bounds__(256) late_kernel(const LateParams p) {
             const int y = (int)(o & (NY - 1));
             const float2 a = in[((2 * rp) << p.k) + y];
             const float2 c = in[((2 * rp + 1) << p.k) + y];
-            v[e] = (y & 1) ? make_float2(a.x - c.x, a.y - c.y) : make_float2(a.x + c.x, a.y + c.y);
+            const float2 wc = (y & 1) ? make_float2(c.x * p.w.x - c.y * p.w.y, c.x * p.w.y + c.y * p.w.x) : c;
+            v[e] = make_float2(a.x + wc.x, a.y + wc.y);
         }
         __syncthreads();
         for (int q = 0; q < p.nops; ++q) {
@@ -122,9 +124,11 @@ __global__ void __launch_bounds__(256) late_kernel(const LateParams p) {
                     v[lo] = r0;
                     v[hi] = r1;
                 }
-            } else {
+            } else {  // entangler diag(1, 1, 1, m[0]) on bits j, j+1
+                const float2 w = op.m[0];
                 for (int e = tid; e < len; e += 256)
-                    if (((e >> op.j) & 1) && ((e >> (op.j + 1)) & 1)) v[e] = make_float2(-v[e].x, -v[e].y);
+                    if (((e >> op.j) & 1) && ((e >> (op.j + 1)) & 1))
+                        v[e] = make_float2(v[e].x * w.x - v[e].y * w.y, v[e].x * w.y + v[e].y * w.x);
             }
             __syncthreads();
         }

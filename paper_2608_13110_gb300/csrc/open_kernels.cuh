@@ -28,6 +28,7 @@ struct LateParams {
     int k;
     const OpenOp* ops;     // the segment after this crossing
     int nops;
+    float2 w;              // the crossing's entangler factor (-1 for CZ)
 };
 
 struct OpenFinalParams {

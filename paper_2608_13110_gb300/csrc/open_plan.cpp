@@ -18,7 +18,7 @@
 // multiplied on the left by the late operations that precede the first late
 // crossing (they act on y only, so they commute with the join). Every later
 // crossing l_i contracts sigma_(l_i) (address bit k+i-1):
-//   Z'[y] = sum_s (-1)^(s y_0) Z[s][y],
+//   Z'[y] = sum_s (-1)^(s y_0) Z[s][y]   (w^(s y_0) for an entangler diag(1,1,1,w)),
 // followed by segment i: the band operations after layer l_i up to the band
 // CZs of the next crossing layer (the output slot d after the last one).
 // All of it is computed in FP64 and stored in FP32 for the device.
@@ -49,13 +49,15 @@ struct Band {
             psi[y1] = u.a[2] * a + u.a[3] * b;
         }
     }
-    void cz(int j) {
+    // entangler diag(1, 1, 1, w) on band bits j, j+1 (w = -1: CZ)
+    void cz(int j, cd w) {
         for (size_t y = 0; y < psi.size(); ++y)
-            if (((y >> j) & 1) && ((y >> (j + 1)) & 1)) psi[y] = -psi[y];
+            if (((y >> j) & 1) && ((y >> (j + 1)) & 1)) psi[y] *= w;
     }
-    void z0() {
+    // the crossing entangler with its fixed-region bit equal to 1: w on band bit 0
+    void z0(cd w) {
         for (size_t y = 0; y < psi.size(); ++y)
-            if (y & 1) psi[y] = -psi[y];
+            if (y & 1) psi[y] *= w;
     }
 };
 
@@ -91,14 +93,14 @@ int open_tables(Plan& P, std::string& err) {
         for (int t = 0; t < c; ++t) {
             for (int j = 0; j < k; ++j) band.gate(j, U(q0 + j, t));
             band_cz(t, js);
-            for (int j : js) band.cz(j);
-            if (t % 2 == par && ((s >> (t / 2)) & 1)) band.z0();
+            for (int j : js) band.cz(j, P.w(t, q0 + j));
+            if (t % 2 == par && ((s >> (t / 2)) & 1)) band.z0(P.w(t, q0 - 1));
         }
         // late operations before the first late crossing's contraction
         for (int t = c; t <= l1; ++t) {
             for (int j = 0; j < k; ++j) band.gate(j, U(q0 + j, t));
             band_cz(t, js);
-            for (int j : js) band.cz(j);
+            for (int j : js) band.cz(j, P.w(t, q0 + j));
         }
         for (size_t y = 0; y < B; ++y)
             P.open_E[s * B + y] = make_float2((float)band.psi[y].real(), (float)band.psi[y].imag());
@@ -113,22 +115,26 @@ int open_tables(Plan& P, std::string& err) {
         for (int e = 0; e < 4; ++e) o.m[e] = make_float2((float)u.a[e].real(), (float)u.a[e].imag());
         P.open_ops.push_back(o);
     };
-    auto push_cz = [&](int j) {
+    auto push_cz = [&](int j, cd w) {  // m[0] = w of diag(1, 1, 1, w)
         OpenOp o;
         o.kind = 1;
         o.j = j;
         for (int e = 0; e < 4; ++e) o.m[e] = make_float2(0, 0);
+        o.m[0] = make_float2((float)w.real(), (float)w.imag());
         P.open_ops.push_back(o);
     };
+    P.open_w.clear();
     for (int i = 0; i < nlate; ++i) {
         const int li = l1 + 2 * i;
+        const cd wc = P.w(li, q0 - 1);  // crossing entangler: sum_s w^(s y0) Z[s][y]
+        P.open_w.push_back(make_float2((float)wc.real(), (float)wc.imag()));
         const bool last = i + 1 == nlate;
         const int stop = last ? d : li + 2;  // next crossing layer (its band CZs included)
         for (int t = li + 1; t <= stop; ++t) {
             for (int j = 0; j < k; ++j) push_gate(j, U(q0 + j, t));
             if (t < d) {
                 band_cz(t, js);
-                for (int j : js) push_cz(j);
+                for (int j : js) push_cz(j, P.w(t, q0 + j));
             }
         }
         P.open_seg.push_back((int32_t)P.open_ops.size());

@@ -17,6 +17,9 @@
 // CZ layer l. Because CZ is diagonal, psi(x) is a sum over all s of
 //   prod_q U_(q,0)[s_(q,0),0] prod_(l>=1) U_(q,l)[s_(q,l), s_(q,l-1)] U_(q,d)[x_q, s_(q,d-1)]
 //   * prod over coupled pairs of (-1)^(s_(i,l) s_(i+1,l)).
+// Any diagonal entangler of operator Schmidt rank 2 works the same way
+// (Sec. 2.1 allows them): a controlled phase diag(1, 1, 1, w) replaces the
+// factor (-1)^(s s') by w^(s s'), so every -1 below may be a per-gate w.
 // Qubit q waits for its partner q+1 in the layers L_q = {l : l = q mod 2}.
 // The boundary after row q is indexed by (s_(q,l)), l in L_q, stored at
 // address bit floor(l/2), h = ceil(d/2) bits. For even d every row has h such
@@ -287,7 +290,8 @@ static void sym_alg1(int n, int d, int* width, double* log2cost) {
 // ---------------------------------------------------------------------------
 
 int plan_build(Plan& P, int n, int d, const uint8_t* cliff, const uint8_t* tmask,
-               const tb_gate1q* extra, int n_extra, const tb_opts* opts, std::string& err) {
+               const tb_gate1q* extra, int n_extra, const double* cphase, const tb_opts* opts,
+               std::string& err) {
     if (n < 2 || d < 2 || (d + 1) / 2 > MAX_PLAN_H) {
         err = "the planner needs n >= 2, d >= 2 and ceil(d/2) <= 40";
         return TB_EDOMAIN;
@@ -329,6 +333,16 @@ int plan_build(Plan& P, int n, int d, const uint8_t* cliff, const uint8_t* tmask
     }
     auto U = [&](int q, int t) -> const M2& { return P.U[(size_t)t * n + q]; };
 
+    // ---- entanglers: CZ, or diag(1, 1, 1, e^(i phi)) per gate (phi = pi is CZ exactly)
+    P.W.assign((size_t)d * (n - 1), cd(-1.0, 0.0));
+    if (cphase)
+        for (int l = 0; l < d; ++l)
+            for (int i = l % 2; i + 1 < n; i += 2) {
+                const double phi = cphase[(size_t)l * (n - 1) + i];
+                if (!std::isfinite(phi)) { err = "controlled-phase angles must be finite"; return TB_EINVAL; }
+                P.W[(size_t)l * (n - 1) + i] = phi == M_PI ? cd(-1.0, 0.0) : std::polar(1.0, phi);
+            }
+
     // ---- paired steps of rows 1..n-2
     P.steps.clear(); P.steps64.clear(); P.step_tgt.clear(); P.step_ctl.clear(); P.step_xq.clear();
     P.row_end.clear();
@@ -344,10 +358,13 @@ int plan_build(Plan& P, int n, int d, const uint8_t* cliff, const uint8_t* tmask
                     for (int ap = 0; ap < 2; ++ap)
                         for (int s = 0; s < 2; ++s) {
                             cd acc = 0;
+                            // the consumed layer's entangler with row r-1: 1, or w when s = a = 1
+                            const int lw = fwd ? 2 * p : 2 * p + 1;  // (d itself for the create step)
+                            const cd wl = lw < d ? P.w(lw, r - 1) : cd(1.0);
                             if (odd_d && p == h - 1) {  // sum-out (forward) / create (backward)
                                 if (fwd && ap == 0)
                                     for (int a = 0; a < 2; ++a)
-                                        acc += U(r, d).a[x * 2 + a] * ((s & a) ? -1.0 : 1.0) *
+                                        acc += U(r, d).a[x * 2 + a] * ((s & a) ? wl : cd(1.0)) *
                                                ((p == 0) ? U(r, 0).a[a * 2 + 0] : U(r, 2 * p).a[a * 2 + c]);
                                 if (!fwd && s == 0)
                                     acc = U(r, d).a[x * 2 + ap] * ((p == 0) ? U(r, 0).a[ap * 2 + 0] : cd(1.0));
@@ -356,7 +373,7 @@ int plan_build(Plan& P, int n, int d, const uint8_t* cliff, const uint8_t* tmask
                                 continue;
                             }
                             for (int a = 0; a < 2; ++a) {
-                                const double sg_ = (s & a) ? -1.0 : 1.0;
+                                const cd sg_ = (s & a) ? wl : cd(1.0);
                                 cd left, right;
                                 if (fwd) {
                                     left = U(r, 2 * p + 1).a[ap * 2 + a];
@@ -435,9 +452,10 @@ int plan_build(Plan& P, int n, int d, const uint8_t* cliff, const uint8_t* tmask
     {
         const int r = n - 1;
         auto A = [&](int p, int sbit) {
-            const M2 D = m2(1, 0, 0, sbit ? -1.0 : 1.0);
-            const M2 I2 = m2(1, 0, 0, 1);
             const bool even_coupled = ((n - 2) % 2) == 0;  // L_(n-2) holds even layers
+            const int lc = even_coupled ? 2 * p : 2 * p + 1;  // the coupled layer of this factor
+            const M2 D = m2(1, 0, 0, (sbit && lc < d) ? P.w(lc, n - 2) : cd(1.0));
+            const M2 I2 = m2(1, 0, 0, 1);
             const M2 D0 = even_coupled ? D : I2;             // layer 2p
             const M2 D1 = even_coupled ? I2 : D;             // layer 2p+1
             if (odd_d && p == h - 1) {

@@ -23,6 +23,10 @@ struct Plan {
     int n = 0, d = 0, h = 0;
     tb_opts opts{};
     std::vector<M2> U;  // (d+1)*n folded slot gates, index t*n + q
+    // entangler of pair (i, i+1) in layer l: diag(1, 1, 1, W[l*(n-1) + i])
+    // (-1 for CZ); entries of pairs the layer does not couple are unused
+    std::vector<std::complex<double>> W;
+    std::complex<double> w(int l, int i) const { return W[(size_t)l * (n - 1) + i]; }
     // paired steps of rows 1..n-2 in execution order
     std::vector<StepG> steps;
     std::vector<std::array<std::complex<double>, 16>> steps64;  // the same in FP64
@@ -41,6 +45,7 @@ struct Plan {
     std::vector<float2> open_E;
     std::vector<OpenOp> open_ops;
     std::vector<int32_t> open_seg;
+    std::vector<float2> open_w;  // entangler factor w of each late crossing (-1 for CZ)
     int last_mid_row() const { return open_k ? n - open_k - 1 : n - 2; }
     int n_pass_launches() const {
         return opts.precision != TB_PRECISION_FP32 ? (int)tc_passes.size() : (int)passes.size();
@@ -65,7 +70,8 @@ int open_tables(Plan& P, std::string& err);
 int tc_schedule(Plan& P, std::string& err);
 
 int plan_build(Plan& P, int n, int d, const uint8_t* cliff, const uint8_t* tmask,
-               const tb_gate1q* extra, int n_extra, const tb_opts* opts, std::string& err);
+               const tb_gate1q* extra, int n_extra, const double* cphase, const tb_opts* opts,
+               std::string& err);
 
 }  // namespace tb
 

@@ -294,3 +294,27 @@ def test_autotuner_measures_what_the_device_runs_at_once(tb, monkeypatch):
     autotune.tune(20, nb=16, use_cache=False)
     assert len(seen) == 8
     assert autotune.BATCH_ENTRIES >> 32 == 0  # one width-32 boundary at a time
+
+
+# ------------------------------------------------ controlled-phase entanglers
+
+def test_cphase_plans_validate_angles_and_keep_counters(tb):
+    n, d = 16, 40
+    ph = W.random_phases(n, d, 5)
+    a, b = tb.Plan(n, d).info, tb.Plan(n, d, cphase=ph).info
+    for k in ("width", "log2_cost", "n_steps", "n_passes", "boundary_bytes", "table_bytes"):
+        assert a[k] == b[k], k
+    assert tb.Plan(n, d, cphase=ph, open_k=4).info["open_k"] == 4
+    bad = ph.copy()
+    bad[3, 1] = np.nan  # layer 3 couples (1, 2)
+    with pytest.raises(tb.TbError) as e:
+        tb.Plan(n, d, cphase=bad)
+    assert e.value.status == tb.TB_EINVAL
+    ok = ph.copy()
+    ok[3, 0] = np.nan  # layer 3 does not couple (0, 1): ignored
+    tb.Plan(n, d, cphase=ok)
+    with pytest.raises(ValueError):
+        tb.Plan(n, d, cphase=ph[:, :-1])
+    with pytest.raises(tb.TbError) as e:
+        tb.Plan(n, d, cphase=ph, open_k=11)
+    assert e.value.status == tb.TB_EDOMAIN
