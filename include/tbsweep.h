@@ -165,7 +165,12 @@ TB_API int tb_plan_create_open(int n, int d, const uint8_t* cliff, const uint8_t
  *   open_k: 0 for a plain plan (as tb_plan_create), else the open bits of
  *           tb_plan_create_open with its domain.
  * Other arguments, evaluation and errors as tb_plan_create. Width and cost
- * counters do not depend on the angles. */
+ * counters do not depend on the angles. With one-qubit gates on either side
+ * (folded into the neighbouring slots through extra) this covers every gate
+ * of operator Schmidt rank 2: in the canonical form (A x B) exp(i(c1 XX +
+ * c2 YY + c3 ZZ)) (C x D) rank 2 leaves one nonzero c, which local gates turn
+ * into exp(i c ZZ) = e^(-ic) (Rz(-2c) x Rz(-2c)) diag(1, 1, 1, e^(4ic)),
+ * Rz(t) = diag(e^(-it/2), e^(it/2)). */
 TB_API int tb_plan_create_cphase(int n, int d, const uint8_t* cliff, const uint8_t* tmask,
                                  const tb_gate1q* extra, int n_extra, const double* cphase,
                                  const tb_opts* opts, int open_k, tb_plan** out);

@@ -115,3 +115,19 @@ def test_closed_form_70(tb, oracle_mod, d, prec):
     ref = oracle_mod.closed_form_hdiag(c, bits, ph)
     got = tb.Plan.from_circuit(c, precision=prec, cphase=ph).amplitudes(bits)
     assert rel_l2(got, ref) < BOUND[prec]
+
+
+def test_graph_batch_with_controlled_phases(tb):
+    """Controlled-phase plans are ordinary plans for the batch runtime."""
+    import torch
+    circuits = [W.random_circuit(n, d, None, nb, 2100 + i)
+                for i, (n, d, nb) in enumerate([(10, 27, 3), (14, 30, 2), (6, 9, 5)])]
+    plans = [tb.Plan.from_circuit(c, cphase=W.random_phases(c.n, c.d, 2200 + i)) for i, c in enumerate(circuits)]
+    d_bits = [torch.from_numpy(c.bits).cuda() for c in circuits]
+    d_out = [torch.empty((c.bits.shape[0], 2), dtype=torch.float64, device="cuda") for c in circuits]
+    batch = tb.Batch(list(zip(plans, d_bits, d_out)))
+    batch.launch()
+    torch.cuda.synchronize()
+    for c, p, o in zip(circuits, plans, d_out):
+        got = o.cpu().numpy().view(np.complex128).reshape(-1)
+        np.testing.assert_array_equal(got, p.amplitudes(c.bits))

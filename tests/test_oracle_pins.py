@@ -257,6 +257,41 @@ def test_controlled_phase_closed_form_matches_state_vector(oracle_mod, n, d):
     np.testing.assert_allclose(oracle_mod.closed_form_hdiag(c, bits, ph), ref, atol=1e-13)
 
 
+def test_zz_rotation_is_a_controlled_phase_up_to_one_qubit_gates(oracle_mod):
+    """exp(i c ZZ) = e^(-ic) (Rz(-2c) x Rz(-2c)) diag(1, 1, 1, e^(4ic)): a
+    brickwork of ZZ rotations equals the controlled-phase brickwork with the
+    Rz folded into the next slot (the statement that covers every entangler of
+    operator Schmidt rank 2 up to one-qubit gates)."""
+    n, d = 4, 3
+    u = W.random_unitaries(n, d, 91)
+    c = W.random_phases(n, d, 92) - np.pi
+    rz = lambda t: np.diag([np.exp(-0.5j * t), np.exp(0.5j * t)])
+    # reference: explicit 2^n matrices with exp(i c ZZ) entanglers
+    dim = 1 << n
+    idx = np.arange(dim)
+    state = np.zeros(dim, np.complex128)
+    state[0] = 1.0
+    for t in range(d + 1):
+        m = np.ones((1, 1), np.complex128)
+        for q in reversed(range(n)):
+            m = np.kron(m, u[t, q])
+        state = m @ state
+        if t < d:
+            for i0 in range(t % 2, n - 1, 2):
+                zz = (1 - 2 * ((idx >> i0) & 1)) * (1 - 2 * ((idx >> (i0 + 1)) & 1))
+                state = np.exp(1j * c[t, i0] * zz) * state
+    # controlled phases 4c, Rz(-2c) folded into slot t+1 of both qubits, global phases
+    u2 = u.copy()
+    glob = 1.0 + 0j
+    for t in range(d):
+        for i0 in range(t % 2, n - 1, 2):
+            u2[t + 1, i0] = u2[t + 1, i0] @ rz(-2 * c[t, i0])
+            u2[t + 1, i0 + 1] = u2[t + 1, i0 + 1] @ rz(-2 * c[t, i0])
+            glob *= np.exp(-1j * c[t, i0])
+    got = glob * oracle_mod.sv_state(n, d, u2, 4 * c)
+    np.testing.assert_allclose(got, state, atol=1e-13)
+
+
 # ---------------------------------------------------------------- log-XEB
 
 def test_log_xeb_definition(oracle_mod):
