@@ -157,3 +157,19 @@ def test_batched_sampling_draws_from_the_conditional(tb, oracle_mod):
         lo = cdf[i, b - 1] if b > 0 else 0.0
         assert lo - 1e-4 <= u[i] <= cdf[i, b] + 1e-4
         assert abs(amps[i] - psi[oracle_mod.basis_index(bits[i:i + 1])[0]]) < 1e-5 * np.abs(psi).max() + 1e-6
+
+
+def test_closed_form_70_64_in_the_benchmark_launch(tb, oracle_mod):
+    """The open workload's launch configuration at full size: n = 70, d = 64,
+    k = 8, two prefixes side by side, windows 9 / bottom 10 / top 7 (the
+    autotuner's choice at width 32): every suffix of both prefixes against the
+    closed form of an H / diagonal / H circuit."""
+    from test_gpu_parity import _nonzero_bits
+    c = W.hdiag_circuit(70, 64, 426, 0, 4100)
+    k = 8
+    prefixes = _nonzero_bits(c, oracle_mod, 2, 11)[:, : c.n - k]
+    plan = tb.Plan.from_circuit(c, open_k=k, window_bits=9, bottom_bits=10, top_bits=7)
+    got = plan.amplitudes(prefixes)
+    ref = oracle_mod.closed_form_hdiag(c, full_bits(prefixes, c.n, k)).reshape(2, -1)
+    for a in range(2):
+        assert rel_l2(got[a], ref[a]) < TOL
