@@ -199,6 +199,62 @@ def test_closed_form_product_when_d_is_0_mod_4(oracle_mod):
     np.testing.assert_allclose(oracle_mod.closed_form_hdiag(c, bits), exp, rtol=1e-12, atol=0)
 
 
+@pytest.mark.parametrize("d", [63, 65])
+def test_closed_form_pair_product_for_odd_d(oracle_mod, d):
+    """For odd d, edge (i, i+1) sees ceil(d/2) CZ layers when i is even and
+    floor(d/2) when i is odd, so exactly one parity of edges keeps a CZ and the
+    amplitude at n = 70 is a product of disjoint pair factors (and single-qubit
+    factors at the chain ends), each a four-term sum written out here:
+    f(x_a, x_b) = 1/4 sum_(y,y') e^(i(th_a y + th_b y')) (-1)^(y y' + x_a y + x_b y')."""
+    n = 70
+    c = W.hdiag_circuit(n, d, int(round(0.095 * n * d)), 6, 8 + d)
+    tab = oracle_mod.clifford_table()
+    theta = np.zeros(n)
+    for t in range(1, d):
+        theta += np.angle(tab[c.cliff[t].astype(int), 1, 1])
+    theta += np.pi / 4 * c.tmask.sum(axis=0)
+    kept = 0 if ((d + 1) // 2) % 2 == 1 else 1  # parity of the edges with an odd CZ count
+    assert ((d + 1) // 2 if kept == 0 else d // 2) % 2 == 1
+
+    def single(th, x):
+        return (1 + np.exp(1j * th) * (-1) ** x) / 2
+
+    def pair(ta, tb, xa, xb):
+        tot = 0
+        for y in (0, 1):
+            for yp in (0, 1):
+                tot += np.exp(1j * (ta * y + tb * yp)) * (-1) ** (y * yp + xa * y + xb * yp)
+        return tot / 4
+
+    groups = ([(0,)] if kept == 1 else []) + [(q, q + 1) for q in range(kept, n - 1, 2)]
+    if groups[-1][-1] < n - 1:
+        groups.append((n - 1,))
+
+    def factor(g, x):
+        return single(theta[g[0]], x[g[0]]) if len(g) == 1 else pair(theta[g[0]], theta[g[1]], x[g[0]], x[g[1]])
+
+    # bitstrings whose factors are all far from zero, so that the comparison is
+    # relative: each group takes its largest factor, or on a random fifth of
+    # the groups its second largest
+    rng = np.random.default_rng(d)
+    bits = np.zeros((6, n), np.int64)
+    for b in range(6):
+        for g in groups:
+            opts = []
+            for v in range(1 << len(g)):
+                x = bits[b].copy()
+                for j, q in enumerate(g):
+                    x[q] = (v >> j) & 1
+                opts.append((abs(factor(g, x)), v))
+            opts.sort(reverse=True)
+            v = opts[1][1] if (b > 0 and rng.random() < 0.2) else opts[0][1]
+            for j, q in enumerate(g):
+                bits[b, q] = (v >> j) & 1
+    exp = np.array([np.prod([factor(g, x) for g in groups]) for x in bits])
+    got = oracle_mod.closed_form_hdiag(c, bits.astype(np.uint8))
+    np.testing.assert_allclose(got, exp, rtol=1e-10, atol=0)
+
+
 def test_identity_circuit(oracle_mod):
     for n, d in [(5, 6), (8, 9)]:
         c = W.identity_circuit(n, d, 10, 3)
