@@ -114,7 +114,11 @@ typedef struct {
                                max(h, 2k) (Proposition 2: h for k <= d/4) */
 } tb_plan_info_t;
 
-/* Create a plan (host only: no CUDA call is made).
+/* Create a plan (host only: no CUDA call is made): the circuit of Sec. 2.1
+ * folded into the network of Sec. 2.2 (one-qubit gates absorbed into the
+ * neighbouring tensors), the paired steps of Algorithm 1 for every absorbed
+ * row (Sec. 3.1, Proposition 1), the pass schedule that fuses consecutive
+ * steps of a window of address bits, and the counters W and C.
  *   n, d   : qubits and CZ layers; n >= 2, 2 <= d, ceil(d/2) <= 40 (odd or
  *            even d)
  *            (else TB_EDOMAIN). Plans wider than 33 bits (2^33 complex64 =
@@ -186,12 +190,13 @@ TB_API int tb_plan_create_cphase(int n, int d, const uint8_t* cliff, const uint8
 TB_API int tb_batched_sample(const double* amps, int k, int64_t na, const double* u, int32_t* b,
                              double* q);
 
-/* Fill *info. */
+/* Fill *info: sizes of the plan and Algorithm 1's counters (Sec. 2.2). */
 TB_API int tb_plan_info(const tb_plan* plan, tb_plan_info_t* info);
 
 /* Device workspace bytes that tb_amplitudes / tb_amplitudes_device need to
  * evaluate nb bitstrings (tables, rescaling state, partial sums and one
- * boundary per bitstring evaluated concurrently). Returns -1 on a bad
+ * boundary per bitstring evaluated concurrently: the temporal state of
+ * Sec. 3.1 is 2^h complex64). Returns -1 on a bad
  * argument. The batch a call evaluates concurrently is the largest that fits
  * the workspace given (and the plan's hbm_budget_bytes). */
 TB_API int64_t tb_workspace_bytes(const tb_plan* plan, int64_t nb);
@@ -207,7 +212,8 @@ TB_API int64_t tb_workspace_min_bytes(const tb_plan* plan);
  *   stream: a cudaStream_t, or NULL for the legacy default stream. */
 TB_API int tb_plan_upload(const tb_plan* plan, void* d_ws, int64_t ws_bytes, void* stream);
 
-/* Amplitudes from device-resident inputs, fully asynchronous on stream.
+/* Amplitudes psi(x) = <x|U|0^n> (Sec. 2.2) by Algorithm 1 (Sec. 3.1) from
+ * device-resident inputs, fully asynchronous on stream.
  *   d_bits: device, nb*n bytes, d_bits[i*n + q] = x_q in {0,1} (values are
  *           not checked on the device; anything nonzero counts as 1).
  *   d_ws  : workspace that tb_plan_upload filled for this plan.
@@ -216,7 +222,8 @@ TB_API int tb_plan_upload(const tb_plan* plan, void* d_ws, int64_t ws_bytes, voi
 TB_API int tb_amplitudes_device(const tb_plan* plan, const uint8_t* d_bits, int64_t nb,
                          void* d_ws, int64_t ws_bytes, double* d_out, void* stream);
 
-/* Amplitudes end to end from host buffers: uploads the tables, copies the
+/* Amplitudes psi(x) = <x|U|0^n> (Sec. 2.2, Algorithm 1) end to end from host
+ * buffers: uploads the tables, copies the
  * bitstrings host->device, runs the sweep, copies the amplitudes back and
  * synchronises the stream before returning.
  *   bits : host, nb*n bytes in {0,1} (checked: TB_EINVAL otherwise).
@@ -227,7 +234,8 @@ TB_API int tb_amplitudes_device(const tb_plan* plan, const uint8_t* d_bits, int6
 TB_API int tb_amplitudes(const tb_plan* plan, const uint8_t* bits, int64_t nb, void* d_ws,
                   int64_t ws_bytes, double* out, void* stream);
 
-/* The pass schedule: for pass i, sched[3*i] = shape (0 forward window,
+/* The pass schedule (the windows in which Algorithm 1's paired steps are
+ * fused; no counterpart in the paper's listing): for pass i, sched[3*i] = shape (0 forward window,
  * 1 reversed window, 2 turn at the top, 3 turn at address bit 0, 4 first
  * window of the first absorbed row, 5 last window of a reversed last row,
  * 6 last window of a forward last row, 7 dense tensor-core block of a
