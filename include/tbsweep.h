@@ -235,7 +235,7 @@ TB_API int tb_amplitudes(const tb_plan* plan, const uint8_t* bits, int64_t nb, v
                   int64_t ws_bytes, double* out, void* stream);
 
 /* The pass schedule (the windows in which Algorithm 1's paired steps are
- * fused; no counterpart in the paper's listing): for pass i, sched[3*i] = shape (0 forward window,
+ * fused into one HBM pass each; the fusion is this library's): for pass i, sched[3*i] = shape (0 forward window,
  * 1 reversed window, 2 turn at the top, 3 turn at address bit 0, 4 first
  * window of the first absorbed row, 5 last window of a reversed last row,
  * 6 last window of a forward last row, 7 dense tensor-core block of a
