@@ -318,3 +318,41 @@ def test_cphase_plans_validate_angles_and_keep_counters(tb):
     with pytest.raises(tb.TbError) as e:
         tb.Plan(n, d, cphase=ph, open_k=11)
     assert e.value.status == tb.TB_EDOMAIN
+
+
+def test_null_and_out_of_range_arguments_fail_without_device_work(tb):
+    """Every entry point that takes host pointers or sizes refuses bad ones
+    with a status (no exception crosses the ABI, no CUDA call is made)."""
+    import ctypes
+    L = tb._lib
+    info = tb._Info()
+    assert L.tb_plan_info(None, ctypes.byref(info)) == tb.TB_EINVAL
+    plan = tb.Plan(8, 10)
+    assert L.tb_plan_info(plan._h, None) == tb.TB_EINVAL
+    assert L.tb_workspace_bytes(None, 1) == -1
+    assert L.tb_workspace_bytes(plan._h, -1) == -1
+    assert L.tb_plan_schedule(None, None, 0) == -1
+    m = (ctypes.c_double * 8)()
+    assert L.tb_clifford_matrix(24, m) == tb.TB_EINVAL
+    assert L.tb_clifford_matrix(-1, m) == tb.TB_EINVAL
+    out = ctypes.c_double(0.0)
+    amps = np.ones(4, np.float64)
+    assert L.tb_log_xeb(None, 2, 10, ctypes.byref(out)) == tb.TB_EINVAL
+    assert L.tb_log_xeb(amps.ctypes.data_as(tb._dp), 0, 10, ctypes.byref(out)) == tb.TB_EINVAL
+    assert L.tb_plan_create(8, 10, None, None, None, 0, None, None) == tb.TB_EINVAL
+    h = tb._vp()
+    assert L.tb_plan_create(8, 10, None, None, None, -1, None, ctypes.byref(h)) == tb.TB_EINVAL
+    assert L.tb_plan_create_cphase(16, 40, None, None, None, 0, None, None, -2, ctypes.byref(h)) == tb.TB_EDOMAIN
+    # the sampler: variates outside [0, 1), k out of range
+    z = np.zeros(2 * 4, np.float64)
+    z[0] = 1.0
+    u = np.array([1.0])
+    b = (ctypes.c_int32 * 1)()
+    assert L.tb_batched_sample(z.ctypes.data_as(tb._dp), 2, 1, u.ctypes.data_as(tb._dp), b, None) == tb.TB_EINVAL
+    u = np.array([0.5])
+    assert L.tb_batched_sample(z.ctypes.data_as(tb._dp), 31, 1, u.ctypes.data_as(tb._dp), b, None) == tb.TB_EINVAL
+    assert L.tb_batched_sample(z.ctypes.data_as(tb._dp), 2, 1, u.ctypes.data_as(tb._dp), b, None) == tb.TB_OK
+    assert b[0] == 0
+    # every status has a message
+    for st in range(0, 7):
+        assert L.tb_status_str(st)
