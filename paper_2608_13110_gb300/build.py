@@ -62,7 +62,15 @@ def build(verbose: bool = False, extra: list[str] | None = None) -> str:
     srcs = sources()
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra), srcs))
-    if os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(o) for o in objs):
+    # relink when an object is newer than the library or the set of sources
+    # changed (a removed source leaves no newer object behind)
+    manifest = LIB + ".objs"
+    listed = ""
+    if os.path.exists(manifest):
+        with open(manifest) as f:
+            listed = f.read()
+    if (os.path.exists(LIB) and listed == "\n".join(objs)
+            and os.path.getmtime(LIB) >= max(os.path.getmtime(o) for o in objs)):
         return LIB
     tmp = LIB + ".tmp"
     cmd = [_nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
@@ -71,6 +79,8 @@ def build(verbose: bool = False, extra: list[str] | None = None) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(manifest, "w") as f:
+        f.write("\n".join(objs))
     if verbose:
         print(LIB)
     return LIB
