@@ -80,6 +80,7 @@ bool small_path(const Plan& P) { return P.h <= SMALL_H_MAX; }
 
 // Set by tb_selftest_bounded_wait for the evaluation it runs on this thread.
 thread_local bool t_tc_selftest = false;
+thread_local bool t_pass_selftest = false;
 
 CallLayout call_layout(const Plan& P) {
     CallLayout c;
@@ -118,15 +119,86 @@ int num_sms() {
     return cached[dev];
 }
 
-cudaError_t launch_pass(const PassDesc& d, const PassParams& p, int grid, cudaStream_t st) {
+// ---- tensor maps of the boundary passes -------------------------------------
+// The pass kernel moves whole tiles with tensor copies. Its map views nbatch
+// consecutive boundaries of 2^h complex64 entries as FP32 elements in five
+// dimensions whose box is one tile (see the slot layout in pass_kernel.cuh):
+//   window at bit 0: [address bits 0..3 (32 floats)][bits 5..12][bit 4]
+//                    [tile index with batch][1];
+//   other windows, C = 13 - M >= 4 low bits, window at bits lo..lo+M-1:
+//     C = 4: [bits 0..3][window bits 0..7][window bit 8][bits 4..lo-1][rest];
+//     C > 4: [bits 0..3][bits 4..C-1][window][bits C..lo-1][rest],
+//   rest = the bits above the window and the batch element.
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled_fn() {
+    static EncodeTiledFn fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<EncodeTiledFn>(f);
+    }();
+    return fn;
+}
+
+bool is_bottom_pass(int type) { return type == P_BOT || type == P_BOT_START || type == P_BOT_END; }
+
+int encode_pass_map(CUtensorMap* m, const PassDesc& d, const float2* B, int h, int64_t nbatch) {
+    EncodeTiledFn enc = encode_tiled_fn();
+    if (!enc) return fail(TB_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    cuuint64_t dim[5];
+    cuuint64_t stride[4];  // bytes, dimensions 1..4
+    cuuint32_t box[5];
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    const cuuint64_t E = 8;  // bytes per entry
+    if (is_bottom_pass(d.type)) {
+        const cuuint64_t tiles = (cuuint64_t)nbatch << (h - TILE_BITS);
+        dim[0] = 32; dim[1] = 256; dim[2] = 2; dim[3] = tiles; dim[4] = 1;
+        stride[0] = 32 * E; stride[1] = 16 * E; stride[2] = (cuuint64_t)TILE * E; stride[3] = (cuuint64_t)TILE * E;
+        box[0] = 32; box[1] = 256; box[2] = 2; box[3] = 1; box[4] = 1;
+    } else {
+        const int M = d.M, lo = d.lo, C = TILE_BITS - M;
+        if (C < 4 || lo < C || lo + M > h) return fail(TB_EINVAL, "pass window outside the tensor-copy layout");
+        const cuuint64_t rest = (cuuint64_t)nbatch << (h - lo - M);
+        dim[0] = 32;
+        stride[2] = (E << C);  // bits C..lo-1
+        stride[3] = (E << (lo + M));
+        dim[3] = (cuuint64_t)1 << (lo - C);
+        dim[4] = rest;
+        box[0] = 32; box[3] = 1; box[4] = 1;
+        if (C == 4) {
+            dim[1] = 256; dim[2] = 2;
+            stride[0] = E << lo; stride[1] = E << (lo + 8);
+            box[1] = 256; box[2] = 2;
+        } else {
+            dim[1] = (cuuint64_t)1 << (C - 4); dim[2] = (cuuint64_t)1 << M;
+            stride[0] = 16 * E; stride[1] = E << lo;
+            box[1] = (cuuint32_t)1 << (C - 4); box[2] = (cuuint32_t)1 << M;
+        }
+    }
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<float2*>(B), dim, stride, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return fail(TB_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ") for a pass of type " +
+                                  std::to_string(d.type) + ", M=" + std::to_string(d.M) + ", lo=" + std::to_string(d.lo));
+    return TB_OK;
+}
+
+cudaError_t launch_pass(const PassDesc& d, const PassParams& p, const CUtensorMap& m, int grid, cudaStream_t st) {
     switch (d.type) {
-        case P_FWD: return launch_pass_t0(d.M, p, grid, st);
-        case P_REV: return launch_pass_t1(d.M, p, grid, st);
-        case P_TOP: return launch_pass_t2(d.M, p, grid, st);
-        case P_BOT: return launch_pass_t3(d.M, p, grid, st);
-        case P_BOT_START: return launch_pass_t4(d.M, p, grid, st);
-        case P_BOT_END: return launch_pass_t5(d.M, p, grid, st);
-        case P_TOP_END: return launch_pass_t6(d.M, p, grid, st);
+        case P_FWD: return launch_pass_t0(d.M, p, m, grid, st);
+        case P_REV: return launch_pass_t1(d.M, p, m, grid, st);
+        case P_TOP: return launch_pass_t2(d.M, p, m, grid, st);
+        case P_BOT: return launch_pass_t3(d.M, p, m, grid, st);
+        case P_BOT_START: return launch_pass_t4(d.M, p, m, grid, st);
+        case P_BOT_END: return launch_pass_t5(d.M, p, m, grid, st);
+        case P_TOP_END: return launch_pass_t6(d.M, p, m, grid, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -233,11 +305,11 @@ int run_device(const Plan& P, const uint8_t* d_bits, int64_t nb, void* d_ws, int
                 TB_CUDA(launch_tc_pass(P.opts.precision, tp, grid, st));
             }
         }
+        int* fault = P.passes.empty() ? nullptr : device_fault_word();
+        if (!P.passes.empty() && !fault) return fail(TB_ECUDA, "device fault word not found");
         for (size_t k = 0; k < P.passes.size(); ++k) {
             const PassDesc& d = P.passes[k];
             PassParams pp;
-            pp.B = boundary;
-            pp.b_stride = b_stride;
             pp.h = P.h; pp.lo = d.lo; pp.n = xstride;
             pp.tile_shift = P.h - TILE_BITS;
             pp.ntiles = (int64_t)nbat << pp.tile_shift;
@@ -249,9 +321,14 @@ int run_device(const Plan& P, const uint8_t* d_bits, int64_t nb, void* d_ws, int
             pp.exps = exps;
             pp.sstride = sstride;
             pp.slot = (int)k;
+            pp.fault = fault;
+            pp.selftest = t_pass_selftest ? 1 : 0;
+            CUtensorMap tmap;
+            const int rc = encode_pass_map(&tmap, d, boundary, P.h, nbat);
+            if (rc != TB_OK) return rc;
             const int grid = (int)std::min<int64_t>(pp.ntiles, (int64_t)PASS_CTAS_PER_SM * nsm);  // persistent CTAs
             ProfScope ps(PC_PASS, 16.0 * (double)nbat * (double)b_stride, st);
-            TB_CUDA(launch_pass(d, pp, grid, st));
+            TB_CUDA(launch_pass(d, pp, tmap, grid, st));
         }
 
         if (P.open_k) {  // Algorithm 2: join, late crossings, FP64 output

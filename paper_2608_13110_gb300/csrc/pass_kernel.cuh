@@ -7,27 +7,44 @@
 //
 // A pass applies a compile-time sequence of controlled 2x2 steps to every
 // tile of 2^13 complex64 entries: the window's M address bits plus 13-M low
-// address bits (the 13 lowest bits when the window starts at bit 0). Each of
-// the 256 threads holds 32 entries; one CTA per SM. A step acts on a
-// 5-bit "register run" of the tile; between runs the tile is re-read from
-// shared memory (XOR-swizzled, conflict-free for every run base used). Tiles
-// stream in through a 3-stage cp.async ring; stores go from registers
-// straight to HBM with 8 or more consecutive entries on consecutive lanes.
+// address bits (the 13 lowest bits when the window starts at bit 0).
+//
+// Warp-specialised, one persistent CTA per SM:
+//   * one producer thread moves whole tiles between HBM and a 3-stage ring of
+//     shared-memory stages with tensor copies (cp.async.bulk.tensor, 128-byte
+//     swizzle): a load completes on the stage's "full" mbarrier; once the
+//     consumers have written the stage back it is stored in place with one
+//     bulk tensor store, and as soon as the store has read the stage the next
+//     tile's load is issued into it;
+//   * 256 consumer threads (8 warps, 32 entries each) never touch global
+//     memory: each reads a 5-bit "register run" of the tile from the stage,
+//     applies the steps on registers (re-reading the tile under another run
+//     between runs, in place, behind a consumer-only named barrier), writes
+//     its last run back to the stage and arrives on the stage's "done"
+//     mbarrier. HBM reads and writes therefore proceed while the consumers
+//     compute, instead of alternating with the arithmetic.
+// The tensor map orders the tile's address bits so that every register run
+// is read and written without shared-memory bank conflicts (see slot_of).
 //
 // Rescaling: the producer of this pass's input left max(|re|,|im|) of its
 // output in maxs[slot]; this pass multiplies its input by 2^s (exact; folded
 // into the first step's coefficients) with s chosen so that the maximum lands
 // in [0.5, 1), records s in exps[slot+1] and writes its own output maximum to
 // maxs[slot+1].
+//
+// Every mbarrier wait is bounded. A wait that gives up counts once per CTA in
+// the device fault word, the consumers stop together (a barrier reduction
+// decides for all of them), and the producer waits (bounded) for the tile
+// copies it still has in flight before the CTA exits.
 #pragma once
+
+#include <cuda.h>
 
 #include "tb_internal.h"
 
 namespace tb {
 
 struct PassParams {
-    float2* B;            // boundary of batch element 0
-    int64_t b_stride;     // complex entries between batch elements
     int h, lo, n;
     int tile_shift;       // log2(tiles per batch element) = h - TILE_BITS
     int64_t ntiles;       // nbatch << tile_shift
@@ -38,6 +55,8 @@ struct PassParams {
     int32_t* exps;        // exps[b*sstride + slot]
     int64_t sstride;
     int slot;             // slot read; slot+1 written
+    int* fault;           // device word: bounded waits that gave up (one per CTA)
+    int selftest;         // 1: the producer issues no copies, so every wait gives up
 };
 
 __host__ __device__ constexpr bool in_run(int s, int r) { return s >= r && s < r + REG_BITS; }
@@ -52,8 +71,7 @@ struct Shape {
     static constexpr int RA = BOT ? 0 : C;
     static constexpr int RB = BOT ? 5 : TILE_BITS - REG_BITS;
     // the tile arrives in shared memory, so the first run is the one holding
-    // step 0's target; the last run must give coalesced stores from registers
-    // (run 0 would put 32 consecutive entries in one thread)
+    // step 0's target
     static constexpr int first_run() {
         return in_run(C + step_spec(TYPE, M, 0).t, RA) ? RA : RB;
     }
@@ -66,7 +84,6 @@ struct Shape {
         }
         return cur;
     }
-    static constexpr int last_run() { return BOT ? RB : run_of(NS - 1); }
     static constexpr bool valid() {
         if (M < MIN_WINDOW || M > (BOT ? MAX_WINDOW : MAX_WINDOW_HIGH)) return false;
         for (int j = 0; j < NS; ++j)
@@ -81,22 +98,34 @@ __device__ __forceinline__ uint32_t run_base(int r, uint32_t tid) {
     return (tid & ((1u << r) - 1u)) | ((tid >> r) << (r + REG_BITS));
 }
 
-// Shared-memory slot of tile coordinate idx. Bit 0 is never moved, so 16-byte
-// chunks (two entries) stay intact for cp.async; bits 1..3 are XORed with
-// bits 6, 7 and 5^8. For every register run used here (bases 0, 3..8) the 16
-// lanes of a half warp then hit 16 different 8-byte bank pairs (runs >= 3,
-// 8-byte accesses), and for run 0, read as 16-byte pairs, the 8 lanes of a
-// quarter warp hit 8 different 16-byte bank groups.
-__host__ __device__ __forceinline__ constexpr uint32_t swz(uint32_t idx) {
-    return idx ^ (((idx >> 6) & 1u) << 1) ^ (((idx >> 7) & 1u) << 2) ^ ((((idx >> 5) ^ (idx >> 8)) & 1u) << 3);
-}
-// swz is linear over GF(2): for disjoint bit sets, swz(a | b) = swz(a) ^ swz(b),
-// so a run's 32 slots are the thread's swizzled base XOR compile-time constants.
-template <uint32_t J>
-struct SwzC {
-    static constexpr uint32_t v = swz(J);
-};
+// ---------------------------------------------------------------------------
+// Shared-memory layout of a stage (8-byte slots). The tensor copy writes the
+// box in the order of its dimensions, so the stage position of a tile
+// coordinate is a permutation of its bits, and the 128-byte swizzle then XORs
+// slot bits 1..3 with slot bits 4..6 (16-byte chunk index with the 128-byte
+// row index, stage 1024-byte aligned).
+//   * windows above bit 0 (C >= 4 low bits): identity order. Every run used
+//     (bases C >= 4 and 8) puts tile bits 0..3 on lanes 0..3, so a half warp
+//     covers one 128-byte row: 16 distinct 8-byte bank pairs.
+//   * windows at bit 0: tile bits 0..3, then 5..12, then 4. Run 0 (bits 0..4
+//     in registers, read as 16-byte pairs) has tile bits 5..7 = slot bits 4..6
+//     on the lanes of a quarter warp, which the swizzle turns into 8 distinct
+//     16-byte chunks; run 5 has tile bits 0..3 on lanes 0..3 again.
+// The map is linear over GF(2): for disjoint bit sets slot_of(a | b) =
+// slot_of(a) ^ slot_of(b), so a run's 32 slots are the thread's base slot XOR
+// compile-time constants.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr uint32_t swz128(uint32_t s) { return s ^ (((s >> 4) & 7u) << 1); }
 
+template <bool BOT>
+__host__ __device__ constexpr uint32_t slot_of(uint32_t idx) {
+    return swz128(BOT ? ((idx & 15u) | (((idx >> 5) & 255u) << 4) | (((idx >> 4) & 1u) << 12)) : idx);
+}
+
+template <bool BOT, uint32_t J>
+struct SlotC {
+    static constexpr uint32_t v = slot_of<BOT>(J);
+};
 
 // ---------------------------------------------------------------------------
 // Packed complex arithmetic. A thread's 32 entries of register run R are
@@ -240,40 +269,42 @@ __device__ __forceinline__ void stage_coefficients(const StepG* steps, float2* s
     }
 }
 
-// Registers <-> shared tile for register run R (entry j = k + 16 v at tile
+// Registers <-> shared stage for register run R (entry j = k + 16 v at tile
 // coordinate base | j << R). Run 0 moves the two entries of a 16-byte chunk
-// in one 16-byte access.
-template <int R, int J>
+// in one 16-byte access (tile bit 0 is slot bit 0, never swizzled).
+template <bool BOT, int R, int J>
 __device__ __forceinline__ uint32_t run_slot(uint32_t sb) {
-    return sb ^ SwzC<((uint32_t)J << R)>::v;
+    return sb ^ SlotC<BOT, ((uint32_t)J << R)>::v;
 }
 
-template <int R, int J>
+template <bool BOT, int R, int J>
 __device__ __forceinline__ void smem_read_run(float2 (&P)[16], float2 (&Q)[16], const float2* tile, uint32_t sb) {
     if constexpr (J < 32) {
-        const float2 e = tile[run_slot<R, J>(sb)];
+        const float2 e = tile[run_slot<BOT, R, J>(sb)];
         if constexpr (J < 16) { P[J].x = e.x; Q[J].x = e.y; }
         else                  { P[J - 16].y = e.x; Q[J - 16].y = e.y; }
-        smem_read_run<R, J + 1>(P, Q, tile, sb);
+        smem_read_run<BOT, R, J + 1>(P, Q, tile, sb);
     }
 }
 
-template <int R, int J>
-__device__ __forceinline__ void smem_write_run(const float2 (&P)[16], const float2 (&Q)[16], float2* tile, uint32_t sb) {
+template <bool BOT, int R, int J>
+__device__ __forceinline__ void smem_write_run(const float2 (&P)[16], const float2 (&Q)[16], float2* tile,
+                                               uint32_t sb) {
     if constexpr (J < 32) {
-        tile[run_slot<R, J>(sb)] = J < 16 ? make_float2(P[J & 15].x, Q[J & 15].x) : make_float2(P[J & 15].y, Q[J & 15].y);
-        smem_write_run<R, J + 1>(P, Q, tile, sb);
+        tile[run_slot<BOT, R, J>(sb)] =
+            J < 16 ? make_float2(P[J & 15].x, Q[J & 15].x) : make_float2(P[J & 15].y, Q[J & 15].y);
+        smem_write_run<BOT, R, J + 1>(P, Q, tile, sb);
     }
 }
 
-template <int R>
+template <bool BOT, int R>
 __device__ __forceinline__ void smem_read(float2 (&P)[16], float2 (&Q)[16], const float2* tile, uint32_t tid) {
-    uint32_t sb = swz(run_base(R, tid));
+    uint32_t sb = slot_of<BOT>(run_base(R, tid));
     asm volatile("" : "+r"(sb));
     if constexpr (R == 0) {
 #define TB_RD0(K, V)                                                                                         \
     {                                                                                                        \
-        const float4 e = *reinterpret_cast<const float4*>(tile + run_slot<0, (K) + 16 * (V)>(sb));         \
+        const float4 e = *reinterpret_cast<const float4*>(tile + run_slot<BOT, 0, (K) + 16 * (V)>(sb));    \
         if ((V) == 0) { P[K].x = e.x; Q[K].x = e.y; P[(K) + 1].x = e.z; Q[(K) + 1].x = e.w; }              \
         else          { P[K].y = e.x; Q[K].y = e.y; P[(K) + 1].y = e.z; Q[(K) + 1].y = e.w; }              \
     }
@@ -281,36 +312,52 @@ __device__ __forceinline__ void smem_read(float2 (&P)[16], float2 (&Q)[16], cons
         TB_RD0(0, 1) TB_RD0(2, 1) TB_RD0(4, 1) TB_RD0(6, 1) TB_RD0(8, 1) TB_RD0(10, 1) TB_RD0(12, 1) TB_RD0(14, 1)
 #undef TB_RD0
     } else {
-        smem_read_run<R, 0>(P, Q, tile, sb);
+        smem_read_run<BOT, R, 0>(P, Q, tile, sb);
     }
 }
 
-template <int R>
-__device__ __forceinline__ void smem_write(const float2 (&P)[16], const float2 (&Q)[16], float2* tile, uint32_t tid) {
-    uint32_t sb = swz(run_base(R, tid));
+template <bool BOT, int R>
+__device__ __forceinline__ void smem_write(const float2 (&P)[16], const float2 (&Q)[16], float2* tile,
+                                           uint32_t tid) {
+    uint32_t sb = slot_of<BOT>(run_base(R, tid));
     asm volatile("" : "+r"(sb));
     if constexpr (R == 0) {
 #define TB_WR0(K, V)                                                                                          \
     {                                                                                                         \
         const float4 e = (V) == 0 ? make_float4(P[K].x, Q[K].x, P[(K) + 1].x, Q[(K) + 1].x)                   \
                                   : make_float4(P[K].y, Q[K].y, P[(K) + 1].y, Q[(K) + 1].y);                  \
-        *reinterpret_cast<float4*>(tile + run_slot<0, (K) + 16 * (V)>(sb)) = e;                              \
+        *reinterpret_cast<float4*>(tile + run_slot<BOT, 0, (K) + 16 * (V)>(sb)) = e;                         \
     }
         TB_WR0(0, 0) TB_WR0(2, 0) TB_WR0(4, 0) TB_WR0(6, 0) TB_WR0(8, 0) TB_WR0(10, 0) TB_WR0(12, 0) TB_WR0(14, 0)
         TB_WR0(0, 1) TB_WR0(2, 1) TB_WR0(4, 1) TB_WR0(6, 1) TB_WR0(8, 1) TB_WR0(10, 1) TB_WR0(12, 1) TB_WR0(14, 1)
 #undef TB_WR0
     } else {
-        smem_write_run<R, 0>(P, Q, tile, sb);
+        smem_write_run<BOT, R, 0>(P, Q, tile, sb);
     }
+}
+
+// Barrier of the 256 consumer threads only (named barrier 1); the producer
+// warp never joins it.
+__device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;\n" ::"n"(PASS_CONSUMERS) : "memory"); }
+
+// True on every consumer thread if v is true on any of them.
+__device__ __forceinline__ bool consumer_any(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(PASS_CONSUMERS)
+        : "memory");
+    return r != 0;
 }
 
 // Hand the tile from register run R1 to run R2: every thread writes its
 // entries back to their own slots, then reads the slots of its new run.
-template <int R1, int R2>
+template <bool BOT, int R1, int R2>
 __device__ __forceinline__ void transpose(float2 (&P)[16], float2 (&Q)[16], float2* tile, uint32_t tid) {
-    smem_write<R1>(P, Q, tile, tid);
-    __syncthreads();
-    smem_read<R2>(P, Q, tile, tid);
+    smem_write<BOT, R1>(P, Q, tile, tid);
+    consumer_sync();
+    smem_read<BOT, R2>(P, Q, tile, tid);
 }
 
 template <class SH, int I, int R>
@@ -347,16 +394,10 @@ __device__ __forceinline__ void run_steps(float2 (&P)[16], float2 (&Q)[16], cons
     if constexpr (I < SH::NS) {
         constexpr int R = SH::run_of(I);
         constexpr int RP = (I == 0) ? SH::first_run() : SH::run_of(I - 1);
-        if constexpr (R != RP) transpose<RP, R>(P, Q, tile, tid);
+        if constexpr (R != RP) transpose<SH::BOT, RP, R>(P, Q, tile, tid);
         apply_step<SH, I, R>(P, Q, sc, xmask, scale, tid);
         run_steps<SH, I + 1>(P, Q, sc, xmask, scale, tid, tile);
     }
-}
-
-template <class SH>
-__device__ __forceinline__ int64_t tile_addr(uint32_t idx, int lo) {
-    if constexpr (SH::BOT) return idx;
-    else return (int64_t)(idx & ((1u << SH::C) - 1u)) + ((int64_t)(idx >> SH::C) << lo);
 }
 
 __device__ __forceinline__ void flush_max(float m, uint32_t* dst) {
@@ -373,82 +414,189 @@ __device__ __forceinline__ int rescale_exp(float m) {
     return max(-100, min(100, -e));
 }
 
-__device__ __forceinline__ void cp_async16(float2* sdst, const float2* gsrc) {
-    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(sdst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc) : "memory");
+// ---------------------------------------------------------------------------
+// mbarriers and tensor copies (PTX)
+// ---------------------------------------------------------------------------
+constexpr uint32_t PASS_WAIT_TRIES = 1u << 24;    // far beyond any tile's copy or compute time
+constexpr uint32_t PASS_SELFTEST_TRIES = 1u << 10;
+
+__device__ __forceinline__ uint32_t pass_smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-constexpr int PASS_STAGES = 3;
+__device__ __forceinline__ void pbar_init(uint32_t a, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(a), "r"(count) : "memory");
+}
 
-// Origin (in entries) of tile t of one batch element.
+__device__ __forceinline__ void pbar_arrive(uint32_t a) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(a) : "memory");
+}
+
+__device__ __forceinline__ void pbar_expect_tx(uint32_t a, uint32_t bytes) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(a),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// Bounded wait for the phase with the given parity; false if it gave up.
+__device__ __forceinline__ bool pbar_wait(uint32_t a, uint32_t parity, uint32_t tries) {
+    for (uint32_t it = 0; it < tries; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_tile(uint32_t dst, const CUtensorMap* m, int c3, int c4, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %2, %2, %3, %4}], [%5];\n" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(m)), "r"(0), "r"(c3), "r"(c4), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_store_tile(const CUtensorMap* m, int c3, int c4, uint32_t src) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group [%0, {%1, %1, %1, %2, %3}], [%4];\n" ::"l"(
+            reinterpret_cast<uint64_t>(m)),
+        "r"(0), "r"(c3), "r"(c4), "r"(src)
+        : "memory");
+    asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void tma_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+__device__ __forceinline__ void tma_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+
+// Tensor-map coordinates (dimensions 3 and 4) of global tile gt. Windows at
+// bit 0: dimension 3 is the global tile index. Other windows: dimension 3 =
+// the address bits between the low bits and the window, dimension 4 = the
+// bits above the window and the batch element.
 template <class SH>
-__device__ __forceinline__ int64_t tile_origin(int64_t t, int lo) {
+__device__ __forceinline__ void tile_coords(const PassParams& p, int64_t gt, int& c3, int& c4) {
     if constexpr (SH::BOT) {
-        return t << TILE_BITS;
+        c3 = (int)gt;
+        c4 = 0;
     } else {
-        const int nl = lo - SH::C;
-        return ((t & (((int64_t)1 << nl) - 1)) << SH::C) | ((t >> nl) << (lo + SH::M));
+        const int64_t b = gt >> p.tile_shift;
+        const int64_t t = gt & (((int64_t)1 << p.tile_shift) - 1);
+        const int nl = p.lo - SH::C;
+        c3 = (int)(t & (((int64_t)1 << nl) - 1));
+        c4 = (int)((b << (p.h - p.lo - SH::M)) + (t >> nl));
     }
 }
 
-// Issue the 16-byte copies of tile gt into a stage (4096 chunks, 16 per thread;
-// chunk c = j*256 + tid covers tile coordinates 2c, 2c+1).
-// Chunk c = j*256 + tid: tile coordinate 2*tid + 512*j. The two terms have
-// disjoint bits, so the swizzled slot is swz(2*tid) + 512*j and the HBM offset
-// is tile_addr(2*tid) + tile_addr(512*j) (a per-thread base plus constants).
-template <class SH>
-__device__ __forceinline__ void issue_tile(const PassParams& p, int64_t gt, float2* stage, uint32_t s0,
-                                           int64_t a0) {
-    const int64_t b = gt >> p.tile_shift;
-    const int64_t t = gt & (((int64_t)1 << p.tile_shift) - 1);
-    const float2* base = p.B + b * p.b_stride + tile_origin<SH>(t, p.lo) + a0;
-    const int64_t st = tile_addr<SH>(2u * PASS_THREADS, p.lo);  // HBM offset of j = 1
-#pragma unroll
-    for (int j = 0; j < TILE / 2 / PASS_THREADS; ++j)
-        cp_async16(stage + s0 + 2u * PASS_THREADS * j, base + j * st);
-}
-
+constexpr int PASS_STAGES = 3;
+constexpr uint32_t TILE_BYTES = (uint32_t)TILE * 8u;
 
 template <int TYPE, int M>
-__global__ void __launch_bounds__(PASS_THREADS, PASS_CTAS_PER_SM) pass_kernel(const PassParams p) {
+constexpr int pass_smem_bytes() {
+    return 1024 + PASS_STAGES * TILE * 8 + pass_nsteps(TYPE, M) * 2 * CO * 8 + 2 * PASS_STAGES * 8 + 16;
+}
+
+template <int TYPE, int M>
+__global__ void __launch_bounds__(PASS_THREADS, PASS_CTAS_PER_SM)
+    pass_kernel(const PassParams p, const __grid_constant__ CUtensorMap tmap) {
     using SH = Shape<TYPE, M>;
     static_assert(SH::valid(), "invalid pass shape");
     static_assert(SH::NS <= 32, "step mask holds 32 steps");
     constexpr int NS = SH::NS;
-    extern __shared__ __align__(16) float2 smem[];
-    float2* sc = smem + PASS_STAGES * TILE;
+    extern __shared__ __align__(16) uint8_t dsm[];
+    uint8_t* base = dsm + ((1024u - (pass_smem_u32(dsm) & 1023u)) & 1023u);
+    float2* stages = reinterpret_cast<float2*>(base);
+    float2* sc = stages + PASS_STAGES * TILE;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sc + NS * 2 * CO);  // full[3], done[3]
+    int* s_abort = reinterpret_cast<int*>(bars + 2 * PASS_STAGES);
     const uint32_t tid = threadIdx.x;
+    const uint32_t full0 = pass_smem_u32(bars), done0 = full0 + 8 * PASS_STAGES;
+    const uint32_t stage0 = pass_smem_u32(stages);
 
     stage_coefficients<SH>(p.steps, sc, tid);
+    if (tid == 0) {
+        for (int s = 0; s < PASS_STAGES; ++s) {
+            pbar_init(full0 + 8 * s, 1);
+            pbar_init(done0 + 8 * s, PASS_CONSUMERS);
+        }
+        *s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
 
-    // per-thread parts of the tile copy addresses (see issue_tile)
-    const uint32_t cs0 = swz(2u * tid);
-    const int64_t ca0 = tile_addr<SH>(2u * tid, p.lo);
-    // prologue: the first PASS_STAGES-1 tiles of this CTA
-#pragma unroll
-    for (int s = 0; s < PASS_STAGES - 1; ++s) {
-        const int64_t gt = blockIdx.x + (int64_t)s * gridDim.x;
-        if (gt < p.ntiles) issue_tile<SH>(p, gt, smem + s * TILE, cs0, ca0);
-        cp_async_commit();
+    const int64_t first = blockIdx.x;
+    const int64_t ntl = first < p.ntiles ? (p.ntiles - 1 - first) / gridDim.x + 1 : 0;  // tiles of this CTA
+    const uint32_t tries = p.selftest ? PASS_SELFTEST_TRIES : PASS_WAIT_TRIES;
+
+    static_assert(PASS_THREADS - PASS_CONSUMERS == 128, "one producer warpgroup");
+    static_assert((PASS_THREADS - PASS_CONSUMERS) * PASS_PRODUCER_REGS + PASS_CONSUMERS * PASS_CONSUMER_REGS <=
+                      PASS_THREADS * (65536 / PASS_THREADS / 8 * 8),
+                  "register split exceeds the launch's registers");
+    if (tid >= PASS_CONSUMERS) {
+        // ---------------- producer: one thread of the last warpgroup
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(PASS_PRODUCER_REGS));
+        if (tid != PASS_CONSUMERS) return;
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
+        int64_t last_load[PASS_STAGES];  // tile index k of the latest load per stage (-1: none)
+        for (int st = 0; st < PASS_STAGES; ++st) last_load[st] = -1;
+        if (!p.selftest) {
+            for (int64_t k = 0; k < ntl && k < PASS_STAGES; ++k) {
+                int c3, c4;
+                tile_coords<SH>(p, first + k * gridDim.x, c3, c4);
+                pbar_expect_tx(full0 + 8 * (int)k, TILE_BYTES);
+                tma_load_tile(stage0 + (uint32_t)k * TILE_BYTES, &tmap, c3, c4, full0 + 8 * (int)k);
+                last_load[k] = k;
+            }
+        }
+        int s = 0;
+        uint32_t ph = 0;
+        for (int64_t k = 0; k < ntl; ++k) {
+            if (!pbar_wait(done0 + 8 * s, ph, tries)) {
+                if (atomicExch(s_abort, 1) == 0) atomicAdd(p.fault, 1);
+                break;
+            }
+            int c3, c4;
+            tile_coords<SH>(p, first + k * gridDim.x, c3, c4);
+            tma_store_tile(&tmap, c3, c4, stage0 + (uint32_t)s * TILE_BYTES);
+            if (k + PASS_STAGES < ntl) {
+                tma_wait_read_all();  // the store has read the stage
+                tile_coords<SH>(p, first + (k + PASS_STAGES) * gridDim.x, c3, c4);
+                pbar_expect_tx(full0 + 8 * s, TILE_BYTES);
+                tma_load_tile(stage0 + (uint32_t)s * TILE_BYTES, &tmap, c3, c4, full0 + 8 * s);
+                last_load[s] = k + PASS_STAGES;
+            }
+            if (++s == PASS_STAGES) { s = 0; ph ^= 1u; }
+        }
+        tma_wait_all();
+        if (*(volatile int*)s_abort) {
+            // loads still in flight must land before the CTA's shared memory goes
+            for (int st = 0; st < PASS_STAGES; ++st)
+                if (last_load[st] >= 0)
+                    (void)pbar_wait(full0 + 8 * st, (uint32_t)((last_load[st] / PASS_STAGES) & 1), PASS_WAIT_TRIES);
+        }
+        return;
     }
 
-    const int64_t tmask = ((int64_t)1 << p.tile_shift) - 1;
+    // ---------------- consumers (tid < 256)
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;\n" ::"n"(PASS_CONSUMER_REGS));
     float runmax = 0.0f;
     int64_t cur_b = -1;
     int cur_s = 0;
     float scale = 1.0f;
     uint32_t xmask = 0;
-    int stage = 0;
-    for (int64_t gt = blockIdx.x; gt < p.ntiles; gt += gridDim.x) {
-        {   // keep PASS_STAGES-1 tiles in flight
-            const int64_t nx = gt + (int64_t)(PASS_STAGES - 1) * gridDim.x;
-            const int ns = (stage + PASS_STAGES - 1) % PASS_STAGES;
-            if (nx < p.ntiles) issue_tile<SH>(p, nx, smem + ns * TILE, cs0, ca0);
-            cp_async_commit();
+    const int64_t tmask = ((int64_t)1 << p.tile_shift) - 1;
+    int s = 0;
+    uint32_t ph = 0;
+    for (int64_t k = 0; k < ntl; ++k) {
+        const bool gave_up = !pbar_wait(full0 + 8 * s, ph, tries);
+        if (consumer_any(gave_up)) {
+            if (tid == 0 && atomicExch(s_abort, 1) == 0) atomicAdd(p.fault, 1);
+            break;
         }
+        const int64_t gt = first + k * gridDim.x;
         const int64_t b = gt >> p.tile_shift;
         const int64_t t = gt & tmask;
         if (b != cur_b) {  // per-bitstring state, read once per batch element
@@ -464,85 +612,55 @@ __global__ void __launch_bounds__(PASS_THREADS, PASS_CTAS_PER_SM) pass_kernel(co
         }
         if (t == 0 && tid == 0) p.exps[b * p.sstride + p.slot + 1] = cur_s;
 
-        float2* tile = smem + stage * TILE;
-        cp_async_wait<PASS_STAGES - 1>();
-        __syncthreads();
-
+        float2* tile = stages + s * TILE;
         float2 P[16], Q[16];
-        smem_read<SH::first_run()>(P, Q, tile, tid);
+        smem_read<SH::BOT, SH::first_run()>(P, Q, tile, tid);
         run_steps<SH, 0>(P, Q, sc, xmask, scale, tid, tile);
-        constexpr int RL = SH::run_of(NS - 1);
-        constexpr int RS = SH::last_run();
-        if constexpr (RL != RS) transpose<RL, RS>(P, Q, tile, tid);
 #pragma unroll
-        for (int k = 0; k < 16; ++k)
-            runmax = fmaxf(runmax, fmaxf(fmaxf(fabsf(P[k].x), fabsf(P[k].y)), fmaxf(fabsf(Q[k].x), fabsf(Q[k].y))));
-        {
-            float2* dst = p.B + b * p.b_stride + tile_origin<SH>(t, p.lo);
-            const uint32_t c0 = run_base(RS, tid);
-            int64_t off0 = tile_addr<SH>(c0, p.lo);
-            int64_t st = tile_addr<SH>(1u << RS, p.lo);
-            asm volatile("" : "+l"(off0), "+l"(st));
-#pragma unroll
-            for (int v = 0; v < 2; ++v) {
-#pragma unroll
-                for (int g = 0; g < 2; ++g) {
-                    float2* q = dst + off0 + (int64_t)(16 * v + 8 * g) * st;
-                    asm volatile("" : "+l"(q));
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const int k = 8 * g + j;
-                        q[j * st] = v == 0 ? make_float2(P[k].x, Q[k].x) : make_float2(P[k].y, Q[k].y);
-                    }
-                }
-            }
-        }
-        __syncthreads();  // every thread is done with this stage before it is refilled
-        stage = (stage + 1) % PASS_STAGES;
+        for (int j = 0; j < 16; ++j)
+            runmax = fmaxf(runmax, fmaxf(fmaxf(fabsf(P[j].x), fabsf(P[j].y)), fmaxf(fabsf(Q[j].x), fabsf(Q[j].y))));
+        smem_write<SH::BOT, SH::run_of(NS - 1)>(P, Q, tile, tid);
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // visible to the tensor store
+        pbar_arrive(done0 + 8 * s);
+        if (++s == PASS_STAGES) { s = 0; ph ^= 1u; }
     }
-    cp_async_wait<0>();
     if (cur_b >= 0) flush_max(runmax, p.maxs + cur_b * p.sstride + p.slot + 1);
 }
 
-template <int TYPE, int M>
-constexpr int pass_smem_bytes() {
-    return (PASS_STAGES * TILE + pass_nsteps(TYPE, M) * 2 * CO) * (int)sizeof(float2);
-}
-
 // Launchers, one translation unit per pass type (pass_t<type>.cu).
-cudaError_t launch_pass_t0(int M, const PassParams& p, int grid, cudaStream_t st);
-cudaError_t launch_pass_t1(int M, const PassParams& p, int grid, cudaStream_t st);
-cudaError_t launch_pass_t2(int M, const PassParams& p, int grid, cudaStream_t st);
-cudaError_t launch_pass_t3(int M, const PassParams& p, int grid, cudaStream_t st);
-cudaError_t launch_pass_t4(int M, const PassParams& p, int grid, cudaStream_t st);
-cudaError_t launch_pass_t5(int M, const PassParams& p, int grid, cudaStream_t st);
-cudaError_t launch_pass_t6(int M, const PassParams& p, int grid, cudaStream_t st);
+cudaError_t launch_pass_t0(int M, const PassParams& p, const CUtensorMap& m, int grid, cudaStream_t st);
+cudaError_t launch_pass_t1(int M, const PassParams& p, const CUtensorMap& m, int grid, cudaStream_t st);
+cudaError_t launch_pass_t2(int M, const PassParams& p, const CUtensorMap& m, int grid, cudaStream_t st);
+cudaError_t launch_pass_t3(int M, const PassParams& p, const CUtensorMap& m, int grid, cudaStream_t st);
+cudaError_t launch_pass_t4(int M, const PassParams& p, const CUtensorMap& m, int grid, cudaStream_t st);
+cudaError_t launch_pass_t5(int M, const PassParams& p, const CUtensorMap& m, int grid, cudaStream_t st);
+cudaError_t launch_pass_t6(int M, const PassParams& p, const CUtensorMap& m, int grid, cudaStream_t st);
 
 template <int TYPE, int M>
-cudaError_t launch_one(const PassParams& p, int grid, cudaStream_t st) {
+cudaError_t launch_one(const PassParams& p, const CUtensorMap& m, int grid, cudaStream_t st) {
     if constexpr (!Shape<TYPE, M>::valid()) {
         return cudaErrorInvalidValue;
     } else {
-    constexpr int smem = pass_smem_bytes<TYPE, M>();
-    cudaError_t e = cudaFuncSetAttribute(pass_kernel<TYPE, M>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    pass_kernel<TYPE, M><<<grid, PASS_THREADS, smem, st>>>(p);
-    return cudaGetLastError();
+        constexpr int smem = pass_smem_bytes<TYPE, M>();
+        static_assert(smem <= 227 * 1024, "pass kernel shared memory");
+        cudaError_t e = cudaFuncSetAttribute(pass_kernel<TYPE, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        pass_kernel<TYPE, M><<<grid, PASS_THREADS, smem, st>>>(p, m);
+        return cudaGetLastError();
     }
 }
 
-#define TB_DEFINE_LAUNCH_PASS(TYPE, NAME)                                         \
-    cudaError_t NAME(int M, const PassParams& p, int grid, cudaStream_t st) {    \
-        switch (M) {                                                             \
-            case 5: return launch_one<TYPE, 5>(p, grid, st);                     \
-            case 6: return launch_one<TYPE, 6>(p, grid, st);                     \
-            case 7: return launch_one<TYPE, 7>(p, grid, st);                     \
-            case 8: return launch_one<TYPE, 8>(p, grid, st);                     \
-            case 9: return launch_one<TYPE, 9>(p, grid, st);                     \
-            case 10: return launch_one<TYPE, 10>(p, grid, st);                   \
-            default: return cudaErrorInvalidValue;                               \
-        }                                                                        \
+#define TB_DEFINE_LAUNCH_PASS(TYPE, NAME)                                                      \
+    cudaError_t NAME(int M, const PassParams& p, const CUtensorMap& m, int grid, cudaStream_t st) { \
+        switch (M) {                                                                          \
+            case 5: return launch_one<TYPE, 5>(p, m, grid, st);                               \
+            case 6: return launch_one<TYPE, 6>(p, m, grid, st);                               \
+            case 7: return launch_one<TYPE, 7>(p, m, grid, st);                               \
+            case 8: return launch_one<TYPE, 8>(p, m, grid, st);                               \
+            case 9: return launch_one<TYPE, 9>(p, m, grid, st);                               \
+            case 10: return launch_one<TYPE, 10>(p, m, grid, st);                             \
+            default: return cudaErrorInvalidValue;                                            \
+        }                                                                                     \
     }
 
 }  // namespace tb

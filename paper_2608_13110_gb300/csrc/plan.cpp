@@ -519,9 +519,13 @@ int plan_build(Plan& P, int n, int d, const uint8_t* cliff, const uint8_t* tmask
         const int b_lo = P.opts.bottom_bits ? P.opts.bottom_bits : MIN_WINDOW;
         const int b_hi = P.opts.bottom_bits ? P.opts.bottom_bits : MAX_WINDOW;
         const int t_lo = P.opts.top_bits ? P.opts.top_bits : MIN_WINDOW;
-        const int t_hi = P.opts.top_bits ? P.opts.top_bits : MAX_WINDOW;
-        if (b_lo < MIN_WINDOW || b_hi > MAX_WINDOW || t_lo < MIN_WINDOW || t_hi > MAX_WINDOW) {
-            err = "bottom_bits / top_bits must be in 5..10";
+        const int t_hi = P.opts.top_bits ? P.opts.top_bits : MAX_WINDOW_HIGH;
+        if (b_lo < MIN_WINDOW || b_hi > MAX_WINDOW) {
+            err = "bottom_bits must be in 5..10";
+            return TB_EINVAL;
+        }
+        if (t_lo < MIN_WINDOW || t_hi > MAX_WINDOW_HIGH) {
+            err = "top_bits must be in 5..9";
             return TB_EINVAL;
         }
         double best = 1e300;

@@ -11,12 +11,15 @@ namespace tb {
 // the window's address bits plus enough low address bits for coalescing.
 constexpr int TILE_BITS = 13;
 constexpr int TILE = 1 << TILE_BITS;
-constexpr int PASS_THREADS = 256;     // 8 warps, 32 entries per thread
+constexpr int PASS_CONSUMERS = 256;   // 8 consumer warps, 32 entries per thread
+constexpr int PASS_THREADS = PASS_CONSUMERS + 128;  // + one producer warpgroup (tensor copies)
+constexpr int PASS_PRODUCER_REGS = 40;   // setmaxnreg split of the 168 registers per thread at launch:
+constexpr int PASS_CONSUMER_REGS = 224;  // 128 x 40 + 256 x 224 <= 384 x 168
 constexpr int PASS_CTAS_PER_SM = 1;
 constexpr int REG_BITS = 5;           // entries per thread = 2^REG_BITS
 constexpr int MIN_WINDOW = 5;
 constexpr int MAX_WINDOW = 10;        // window at address bit 0 (whole tile is low bits)
-constexpr int MAX_WINDOW_HIGH = TILE_BITS - 3;  // other windows keep >= 8 consecutive entries
+constexpr int MAX_WINDOW_HIGH = TILE_BITS - 4;  // other windows keep >= 16 consecutive entries (128 B)
 // Boundaries of width <= SMALL_H_MAX live in one CTA's shared memory for the
 // whole sweep (one CTA per bitstring).
 constexpr int SMALL_H_MAX = 12;

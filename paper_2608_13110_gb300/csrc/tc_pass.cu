@@ -29,6 +29,8 @@
 
 #include <cuda_bf16.h>
 
+#include <mutex>
+
 #include "tc_pass.cuh"
 
 namespace tb {
@@ -445,9 +447,14 @@ cudaError_t launch_tc_pass(int precision, const TcParams& p, int grid, cudaStrea
 }
 
 int* device_fault_word() {
-    void* a = nullptr;
-    if (cudaGetSymbolAddress(&a, g_fault_word) != cudaSuccess) return nullptr;
-    return static_cast<int*>(a);
+    // looked up once per device (the symbol's address does not change)
+    static std::mutex mu;
+    static void* addr[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[dev] && cudaGetSymbolAddress(&addr[dev], g_fault_word) != cudaSuccess) addr[dev] = nullptr;
+    return static_cast<int*>(addr[dev]);
 }
 
 }  // namespace tb

@@ -61,11 +61,12 @@ def test_narrow_random_unitaries(tb, oracle_mod, n, d):
 # ------------------------------------------------------- HBM pass schedule
 
 # (n, d, window_bits, bottom_bits, top_bits): together these schedules use
-# every pass shape with every window size 5..10 (checked on the host in
+# every pass shape with every window size it admits (5..10 at address bit 0,
+# 5..9 elsewhere; checked on the host in
 # tests/test_abi_host.py::test_pass_cases_cover_every_shape).
 PASS_CASES = [
-    (6, 42, 6, 8, 5), (6, 46, 8, 6, 5), (6, 36, 9, 5, 6), (6, 44, 10, 7, 7),
-    (6, 32, 5, 9, 8), (6, 36, 5, 10, 9), (7, 28, 5, 5, 10), (7, 26, 5, 5, 9),
+    (6, 42, 6, 8, 5), (6, 46, 8, 6, 5), (6, 36, 9, 5, 6),
+    (6, 32, 5, 9, 8), (6, 36, 5, 10, 9), (7, 26, 5, 5, 9),
     (7, 26, 5, 6, 8), (7, 26, 5, 7, 7), (7, 26, 5, 8, 6), (7, 26, 5, 9, 5),
     (16, 40, 0, 0, 0), (17, 44, 0, 0, 0),
 ]

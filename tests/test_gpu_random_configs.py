@@ -34,7 +34,7 @@ def draw(i):
     opts = {}
     if rng.random() < 0.5:
         opts = {"window_bits": int(rng.integers(5, 11)), "bottom_bits": int(rng.integers(5, 11)),
-                "top_bits": int(rng.integers(5, 11))}
+                "top_bits": int(rng.integers(5, 10))}
     k = 0
     if h >= 13 and n >= 3 and rng.random() < 0.4:
         k = int(rng.integers(1, min(d // 4, 10, n - 1, 6) + 1))
