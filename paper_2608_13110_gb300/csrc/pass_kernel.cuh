@@ -16,15 +16,17 @@
 //     consumers have written the stage back it is stored in place with one
 //     bulk tensor store, and as soon as the store has read the stage the next
 //     tile's load is issued into it;
-//   * 256 consumer threads (8 warps, 32 entries each) never touch global
-//     memory: each reads a 5-bit "register run" of the tile from the stage,
-//     applies the steps on registers (re-reading the tile under another run
-//     between runs, in place, behind a consumer-only named barrier), writes
-//     its last run back to the stage and arrives on the stage's "done"
-//     mbarrier. HBM reads and writes therefore proceed while the consumers
-//     compute, instead of alternating with the arithmetic.
-// The tensor map orders the tile's address bits so that every register run
-// is read and written without shared-memory bank conflicts (see slot_of).
+//   * 8 consumer warps never touch global memory and never wait for one
+//     another: warp w owns the 1024 entries of the tile that share 3 "warp
+//     bits" and holds them as 32 entries per thread: 5 address bits in
+//     registers, 5 on the lanes. Every window bit is one of these 10, so a
+//     step on a register bit is register arithmetic and a step on a lane bit
+//     exchanges the partner lane's entries with warp shuffles. A warp reads
+//     its entries from the stage once, applies every step, writes them back
+//     and arrives on the stage's "done" mbarrier. HBM traffic, shared-memory
+//     traffic and the arithmetic of different warps all overlap.
+// The tensor map orders the tile's address bits so that every warp access to
+// a stage is free of shared-memory bank conflicts (see slot_of).
 //
 // Rescaling: the producer of this pass's input left max(|re|,|im|) of its
 // output in maxs[slot]; this pass multiplies its input by 2^s (exact; folded
@@ -33,8 +35,8 @@
 // maxs[slot+1].
 //
 // Every mbarrier wait is bounded. A wait that gives up counts once per CTA in
-// the device fault word, the consumers stop together (a barrier reduction
-// decides for all of them), and the producer waits (bounded) for the tile
+// the device fault word; the warp stops (all its lanes decide together), the
+// others then give up too, and the producer waits (bounded) for the tile
 // copies it still has in flight before the CTA exits.
 #pragma once
 
@@ -59,8 +61,18 @@ struct PassParams {
     int selftest;         // 1: the producer issues no copies, so every wait gives up
 };
 
-__host__ __device__ constexpr bool in_run(int s, int r) { return s >= r && s < r + REG_BITS; }
+__device__ __forceinline__ uint32_t pass_smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
 
+// Tile bits (13) of a pass and where a consumer thread holds them.
+//   windows at address bit 0 (tile = the 13 lowest address bits, window
+//   bits 0..M-1, M <= 10): lanes hold tile bits 0..4, registers 5..9, the
+//   warp index 10..12;
+//   other windows (tile bits 0..C-1 = the C >= 4 lowest address bits, tile
+//   bits C..12 = the window): lane bits 0..4 hold tile bits 0, 4, 5, 6, 7,
+//   registers 8..12, the warp index 1..3.
+// Every window bit is a lane or register bit in both cases.
 template <int TYPE_, int M_>
 struct Shape {
     static constexpr int TYPE = TYPE_;
@@ -68,34 +80,30 @@ struct Shape {
     static constexpr bool BOT = TYPE == P_BOT || TYPE == P_BOT_START || TYPE == P_BOT_END;
     static constexpr int NS = pass_nsteps(TYPE, M);
     static constexpr int C = BOT ? 0 : TILE_BITS - M;  // tile bit of window bit 0
-    static constexpr int RA = BOT ? 0 : C;
-    static constexpr int RB = BOT ? 5 : TILE_BITS - REG_BITS;
-    // the tile arrives in shared memory, so the first run is the one holding
-    // step 0's target
-    static constexpr int first_run() {
-        return in_run(C + step_spec(TYPE, M, 0).t, RA) ? RA : RB;
+    static constexpr int REG0 = BOT ? 5 : 8;            // tile bit of register bit 0
+    static constexpr int regpos(int t) { return (t >= REG0 && t < REG0 + REG_BITS) ? t - REG0 : -1; }
+    static constexpr int lanepos(int t) {
+        if (BOT) return t < 5 ? t : -1;
+        return t == 0 ? 0 : (t >= 4 && t < 8) ? t - 3 : -1;
     }
-    // register run in which step i executes
-    static constexpr int run_of(int i) {
-        int cur = first_run();
-        for (int j = 0; j <= i; ++j) {
-            const int s = C + step_spec(TYPE, M, j).t;
-            if (!in_run(s, cur)) cur = (cur == RA) ? RB : RA;
-        }
-        return cur;
-    }
+    static constexpr int tgt(int i) { return C + step_spec(TYPE, M, i).t; }
+    static constexpr int ctl(int i) { return step_spec(TYPE, M, i).c < 0 ? -1 : C + step_spec(TYPE, M, i).c; }
     static constexpr bool valid() {
         if (M < MIN_WINDOW || M > (BOT ? MAX_WINDOW : MAX_WINDOW_HIGH)) return false;
-        for (int j = 0; j < NS; ++j)
-            if (!in_run(C + step_spec(TYPE, M, j).t, run_of(j))) return false;
+        for (int j = 0; j < NS; ++j) {
+            if (regpos(tgt(j)) < 0 && lanepos(tgt(j)) < 0) return false;
+            if (ctl(j) >= 0 && regpos(ctl(j)) < 0 && lanepos(ctl(j)) < 0) return false;
+        }
         return true;
     }
 };
 
-// Tile coordinate of a thread's entries for register run r: the 8 thread-index
-// bits fill the tile bits outside [r, r+5) from the bottom.
-__device__ __forceinline__ uint32_t run_base(int r, uint32_t tid) {
-    return (tid & ((1u << r) - 1u)) | ((tid >> r) << (r + REG_BITS));
+// Tile coordinate of a consumer thread's register entry 0.
+template <bool BOT>
+__device__ __forceinline__ uint32_t thread_base(uint32_t tid) {
+    const uint32_t lane = tid & 31u, warp = tid >> 5;
+    if (BOT) return lane | (warp << 10);
+    return (lane & 1u) | ((lane >> 1) << 4) | (warp << 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -103,16 +111,16 @@ __device__ __forceinline__ uint32_t run_base(int r, uint32_t tid) {
 // box in the order of its dimensions, so the stage position of a tile
 // coordinate is a permutation of its bits, and the 128-byte swizzle then XORs
 // slot bits 1..3 with slot bits 4..6 (16-byte chunk index with the 128-byte
-// row index, stage 1024-byte aligned).
-//   * windows above bit 0 (C >= 4 low bits): identity order. Every run used
-//     (bases C >= 4 and 8) puts tile bits 0..3 on lanes 0..3, so a half warp
-//     covers one 128-byte row: 16 distinct 8-byte bank pairs.
-//   * windows at bit 0: tile bits 0..3, then 5..12, then 4. Run 0 (bits 0..4
-//     in registers, read as 16-byte pairs) has tile bits 5..7 = slot bits 4..6
-//     on the lanes of a quarter warp, which the swizzle turns into 8 distinct
-//     16-byte chunks; run 5 has tile bits 0..3 on lanes 0..3 again.
+// row index, stage 1024-byte aligned). A half warp's 8-byte accesses are free
+// of bank conflicts when its 16 slots differ in bits 0..3 after the swizzle.
+//   * windows above bit 0: identity order. Lanes 0..3 hold tile bits 0, 4,
+//     5, 6 and the warp index bits 1..3, so the swizzled bits 0..3 are
+//     t0, t1^t4, t2^t5, t3^t6: a bijection of the lane bits.
+//   * windows at bit 0: tile bits 0..3, then 5..12, then 4. Lanes 0..3 hold
+//     tile bits 0..3 and registers bits 5..7, so the swizzled bits are
+//     t0, t1^t5, t2^t6, t3^t7: again a bijection of the lane bits.
 // The map is linear over GF(2): for disjoint bit sets slot_of(a | b) =
-// slot_of(a) ^ slot_of(b), so a run's 32 slots are the thread's base slot XOR
+// slot_of(a) ^ slot_of(b), so a thread's 32 slots are its base slot XOR
 // compile-time constants.
 // ---------------------------------------------------------------------------
 __host__ __device__ constexpr uint32_t swz128(uint32_t s) { return s ^ (((s >> 4) & 7u) << 1); }
@@ -128,27 +136,33 @@ struct SlotC {
 };
 
 // ---------------------------------------------------------------------------
-// Packed complex arithmetic. A thread's 32 entries of register run R are
-// j = k + 16 v (k: run bits 0..3, v: run bit 4). They are held "planar" in
-// packed pairs P[k] = (re_k, re_(k+16)), Q[k] = (im_k, im_(k+16)), so that
-// one __ffma2_rn (sm_100+ paired FP32 FMA) advances two entries that share
-// their coefficient. A step on run bit K < 4 with coefficients shared by both
-// lanes needs 8 paired FMAs per pair of packed registers (half the scalar
-// count); a step whose control is run bit 4 uses lane-split coefficients; a
-// step whose target is run bit 4 mixes the two lanes of one packed register.
+// Packed complex arithmetic. A thread's 32 entries are j = k + 16 v (k:
+// register bits 0..3, v: register bit 4). They are held "planar" in packed
+// pairs P[k] = (re_k, re_(k+16)), Q[k] = (im_k, im_(k+16)), so that one
+// __ffma2_rn (sm_100+ paired FP32 FMA) advances two entries that share their
+// coefficient. A register step on bit K < 4 with coefficients shared by both
+// halves needs 8 paired FMAs per pair of packed registers; a step whose
+// control is register bit 4 uses lane-split coefficients; a step whose target
+// is register bit 4 mixes the two halves of one packed register. A step on a
+// lane bit takes the partner lane's packed registers by shuffles and applies
+// the row of G that belongs to this lane's own value of the target bit.
 //
-// Coefficients are staged in shared memory already packed, 24 float2 per
+// Coefficients are staged in shared memory already packed, 48 float2 per
 // (step, bitstring variant):
-//   KIND_F  (target, control < 4 or none): for c in 0,1:
-//           [g00r g00i -g00i g01r g01i -g01i g10r g10i -g10i g11r g11i -g11i],
-//           each broadcast to both lanes
-//   KIND_VC (control = run bit 4): the same 12 values with lane c = control
-//   KIND_VT (target = run bit 4): for c in 0,1: [Ar Ai -Ai Br Bi -Bi],
-//           A = (g00, g11) (own lane), B = (g01, g10) (other lane)
+//   register target, control none / not register bit 4 (KIND_F): for c in
+//     0,1: [g00r g00i -g00i g01r g01i -g01i g10r g10i -g10i g11r g11i -g11i],
+//     each broadcast to both halves
+//   KIND_VC (control = register bit 4): the same 12 values with half c = control
+//   KIND_VT (target = register bit 4): for c in 0,1: [Ar Ai -Ai Br Bi -Bi],
+//     A = (g00, g11) (own half), B = (g01, g10) (other half)
+//   KIND_L (target on a lane): for a (this lane's target value) in 0,1, at
+//     24 a: for c in 0,1: [sr si -si or oi -oi] broadcast, s = G[c][a][a],
+//     o = G[c][a][1-a]; then at 24 a + 12 the same 6 values with half c =
+//     control (control = register bit 4)
 // ---------------------------------------------------------------------------
 constexpr int VBIT = 4;
-constexpr int KIND_F = 0, KIND_VC = 1, KIND_VT = 2;
-constexpr int CO = 24;  // packed coefficients per (step, variant)
+constexpr int KIND_F = 0, KIND_VC = 1, KIND_VT = 2, KIND_L = 3;
+constexpr int CO = 48;  // packed coefficients per (step, variant)
 
 __device__ __forceinline__ float2 f2x(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
@@ -163,19 +177,20 @@ __device__ __forceinline__ void cmac_planar(const float2* cf, float2 aP, float2 
     oQ = fma2(cf[0], aQ, fma2(cf[1], aP, fma2(cf[3], bQ, mul2(cf[4], bP))));
 }
 
-__device__ __forceinline__ void load_cf(float2 (&c)[12], const float2* src, float s) {
+template <int N>
+__device__ __forceinline__ void load_cf(float2 (&c)[N], const float2* src, float s) {
     const float4* s4 = reinterpret_cast<const float4*>(src);
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
+    for (int i = 0; i < N / 2; ++i) {
         const float4 q = s4[i];
         c[2 * i] = make_float2(q.x * s, q.y * s);
         c[2 * i + 1] = make_float2(q.z * s, q.w * s);
     }
 }
 
-// Target run bit K < 4 (pairs of packed registers). CK: -1 none (block 0),
-// 0..3 control run bit (block per pair), 4 control = run bit 4 (lane split),
-// 5 external control (block chosen by the caller).
+// Register target bit K < 4 (pairs of packed registers). CK: -1 none (block
+// 0), 0..3 control register bit (block per pair), 4 control = register bit 4
+// (lane-split block), 5 control on a lane (block chosen by the caller).
 template <int K, int CK>
 __device__ __forceinline__ void step_pairs(float2 (&P)[16], float2 (&Q)[16], const float2 (&c0)[12],
                                            const float2 (&c1)[12]) {
@@ -196,10 +211,10 @@ __device__ __forceinline__ void step_pairs(float2 (&P)[16], float2 (&Q)[16], con
     }
 }
 
-// Target run bit 4: the pair is the two lanes of one packed register.
+// Register target bit 4: the pair is the two halves of one packed register.
 template <int CK>
-__device__ __forceinline__ void step_lanes(float2 (&P)[16], float2 (&Q)[16], const float2 (&c0)[12],
-                                           const float2 (&c1)[12]) {
+__device__ __forceinline__ void step_halves(float2 (&P)[16], float2 (&Q)[16], const float2 (&c0)[12],
+                                            const float2 (&c1)[12]) {
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
         const bool hi = (CK >= 0 && CK < 4) ? (((k >> CK) & 1) != 0) : false;
@@ -211,13 +226,32 @@ __device__ __forceinline__ void step_lanes(float2 (&P)[16], float2 (&Q)[16], con
     }
 }
 
+// Lane target (partner lane = lane ^ LM): out = s * own + o * partner. CK as
+// for step_pairs; c0 / c1 hold [sr si -si or oi -oi] for control 0 / 1.
+template <int CK>
+__device__ __forceinline__ void step_lane(float2 (&P)[16], float2 (&Q)[16], const float2 (&c0)[6],
+                                          const float2 (&c1)[6], int LM) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const bool hi = (CK >= 0 && CK < 4) ? (((k >> CK) & 1) != 0) : false;
+        float2 pp, qp;
+        pp.x = __shfl_xor_sync(0xffffffffu, P[k].x, LM);
+        pp.y = __shfl_xor_sync(0xffffffffu, P[k].y, LM);
+        qp.x = __shfl_xor_sync(0xffffffffu, Q[k].x, LM);
+        qp.y = __shfl_xor_sync(0xffffffffu, Q[k].y, LM);
+        float2 op, oq;
+        if (hi) cmac_planar(c1, P[k], Q[k], pp, qp, op, oq);
+        else    cmac_planar(c0, P[k], Q[k], pp, qp, op, oq);
+        P[k] = op; Q[k] = oq;
+    }
+}
+
 template <class SH>
 __host__ __device__ constexpr int step_kind(int i) {
-    const StepSpec sp = step_spec(SH::TYPE, SH::M, i);
-    const int R = SH::run_of(i);
-    const int K = SH::C + sp.t - R;
+    const int K = SH::regpos(SH::tgt(i));
+    if (K < 0) return KIND_L;
     if (K == VBIT) return KIND_VT;
-    if (sp.c >= 0 && in_run(SH::C + sp.c, R) && SH::C + sp.c - R == VBIT) return KIND_VC;
+    if (SH::ctl(i) >= 0 && SH::regpos(SH::ctl(i)) == VBIT) return KIND_VC;
     return KIND_F;
 }
 
@@ -236,6 +270,7 @@ __device__ __forceinline__ void stage_coefficients(const StepG* steps, float2* s
         const int i = w >> 1, x = w & 1;
         const float2* g = steps[i].g[x];  // [c*4 + a'*2 + s]
         float2* o = sc + w * CO;
+        for (int e = 0; e < CO; ++e) o[e] = make_float2(0.f, 0.f);
         const int kind = (int)((KINDS >> (2 * i)) & 3u);
         if (kind == KIND_F) {
             for (int c = 0; c < 2; ++c)
@@ -252,151 +287,105 @@ __device__ __forceinline__ void stage_coefficients(const StepG* steps, float2* s
                 o[3 * e + 1] = make_float2(z0.y, z1.y);
                 o[3 * e + 2] = make_float2(-z0.y, -z1.y);
             }
-            for (int e = 12; e < 24; ++e) o[e] = make_float2(0.f, 0.f);
-        } else {
+        } else if (kind == KIND_VT) {
             for (int c = 0; c < 2; ++c) {
-                const float2 A0 = g[c * 4 + 0], A1 = g[c * 4 + 3];  // own lane: g00 (lo), g11 (hi)
-                const float2 B0 = g[c * 4 + 1], B1 = g[c * 4 + 2];  // other lane: g01 (lo), g10 (hi)
+                const float2 A0 = g[c * 4 + 0], A1 = g[c * 4 + 3];  // own half: g00 (lo), g11 (hi)
+                const float2 B0 = g[c * 4 + 1], B1 = g[c * 4 + 2];  // other half: g01 (lo), g10 (hi)
                 o[c * 12 + 0] = make_float2(A0.x, A1.x);
                 o[c * 12 + 1] = make_float2(A0.y, A1.y);
                 o[c * 12 + 2] = make_float2(-A0.y, -A1.y);
                 o[c * 12 + 3] = make_float2(B0.x, B1.x);
                 o[c * 12 + 4] = make_float2(B0.y, B1.y);
                 o[c * 12 + 5] = make_float2(-B0.y, -B1.y);
-                for (int e = 6; e < 12; ++e) o[c * 12 + e] = make_float2(0.f, 0.f);
+            }
+        } else {
+            for (int a = 0; a < 2; ++a) {
+                float2* oa = o + 24 * a;
+                for (int c = 0; c < 2; ++c) {
+                    const float2 sv = g[c * 4 + a * 2 + a], ov = g[c * 4 + a * 2 + (1 - a)];
+                    const float v[6] = {sv.x, sv.y, -sv.y, ov.x, ov.y, -ov.y};
+                    for (int e = 0; e < 6; ++e) {
+                        oa[c * 6 + e] = f2x(v[e]);
+                        if (c == 0) oa[12 + e].x = v[e];
+                        else        oa[12 + e].y = v[e];
+                    }
+                }
             }
         }
     }
 }
 
-// Registers <-> shared stage for register run R (entry j = k + 16 v at tile
-// coordinate base | j << R). Run 0 moves the two entries of a 16-byte chunk
-// in one 16-byte access (tile bit 0 is slot bit 0, never swizzled).
-template <bool BOT, int R, int J>
-__device__ __forceinline__ uint32_t run_slot(uint32_t sb) {
-    return sb ^ SlotC<BOT, ((uint32_t)J << R)>::v;
-}
-
-template <bool BOT, int R, int J>
-__device__ __forceinline__ void smem_read_run(float2 (&P)[16], float2 (&Q)[16], const float2* tile, uint32_t sb) {
+// Registers <-> shared stage: entry j of a thread sits at tile coordinate
+// thread_base | j << REG0, i.e. slot base ^ SlotC<j << REG0>.
+template <bool BOT, int REG0, int J>
+__device__ __forceinline__ void smem_read_j(float2 (&P)[16], float2 (&Q)[16], const float2* tile, uint32_t sb) {
     if constexpr (J < 32) {
-        const float2 e = tile[run_slot<BOT, R, J>(sb)];
+        const float2 e = tile[sb ^ SlotC<BOT, ((uint32_t)J << REG0)>::v];
         if constexpr (J < 16) { P[J].x = e.x; Q[J].x = e.y; }
         else                  { P[J - 16].y = e.x; Q[J - 16].y = e.y; }
-        smem_read_run<BOT, R, J + 1>(P, Q, tile, sb);
+        smem_read_j<BOT, REG0, J + 1>(P, Q, tile, sb);
     }
 }
 
-template <bool BOT, int R, int J>
-__device__ __forceinline__ void smem_write_run(const float2 (&P)[16], const float2 (&Q)[16], float2* tile,
-                                               uint32_t sb) {
+template <bool BOT, int REG0, int J>
+__device__ __forceinline__ void smem_write_j(const float2 (&P)[16], const float2 (&Q)[16], float2* tile,
+                                             uint32_t sb) {
     if constexpr (J < 32) {
-        tile[run_slot<BOT, R, J>(sb)] =
+        tile[sb ^ SlotC<BOT, ((uint32_t)J << REG0)>::v] =
             J < 16 ? make_float2(P[J & 15].x, Q[J & 15].x) : make_float2(P[J & 15].y, Q[J & 15].y);
-        smem_write_run<BOT, R, J + 1>(P, Q, tile, sb);
+        smem_write_j<BOT, REG0, J + 1>(P, Q, tile, sb);
     }
 }
 
-template <bool BOT, int R>
-__device__ __forceinline__ void smem_read(float2 (&P)[16], float2 (&Q)[16], const float2* tile, uint32_t tid) {
-    uint32_t sb = slot_of<BOT>(run_base(R, tid));
-    asm volatile("" : "+r"(sb));
-    if constexpr (R == 0) {
-#define TB_RD0(K, V)                                                                                         \
-    {                                                                                                        \
-        const float4 e = *reinterpret_cast<const float4*>(tile + run_slot<BOT, 0, (K) + 16 * (V)>(sb));    \
-        if ((V) == 0) { P[K].x = e.x; Q[K].x = e.y; P[(K) + 1].x = e.z; Q[(K) + 1].x = e.w; }              \
-        else          { P[K].y = e.x; Q[K].y = e.y; P[(K) + 1].y = e.z; Q[(K) + 1].y = e.w; }              \
-    }
-        TB_RD0(0, 0) TB_RD0(2, 0) TB_RD0(4, 0) TB_RD0(6, 0) TB_RD0(8, 0) TB_RD0(10, 0) TB_RD0(12, 0) TB_RD0(14, 0)
-        TB_RD0(0, 1) TB_RD0(2, 1) TB_RD0(4, 1) TB_RD0(6, 1) TB_RD0(8, 1) TB_RD0(10, 1) TB_RD0(12, 1) TB_RD0(14, 1)
-#undef TB_RD0
-    } else {
-        smem_read_run<BOT, R, 0>(P, Q, tile, sb);
-    }
-}
-
-template <bool BOT, int R>
-__device__ __forceinline__ void smem_write(const float2 (&P)[16], const float2 (&Q)[16], float2* tile,
-                                           uint32_t tid) {
-    uint32_t sb = slot_of<BOT>(run_base(R, tid));
-    asm volatile("" : "+r"(sb));
-    if constexpr (R == 0) {
-#define TB_WR0(K, V)                                                                                          \
-    {                                                                                                         \
-        const float4 e = (V) == 0 ? make_float4(P[K].x, Q[K].x, P[(K) + 1].x, Q[(K) + 1].x)                   \
-                                  : make_float4(P[K].y, Q[K].y, P[(K) + 1].y, Q[(K) + 1].y);                  \
-        *reinterpret_cast<float4*>(tile + run_slot<BOT, 0, (K) + 16 * (V)>(sb)) = e;                         \
-    }
-        TB_WR0(0, 0) TB_WR0(2, 0) TB_WR0(4, 0) TB_WR0(6, 0) TB_WR0(8, 0) TB_WR0(10, 0) TB_WR0(12, 0) TB_WR0(14, 0)
-        TB_WR0(0, 1) TB_WR0(2, 1) TB_WR0(4, 1) TB_WR0(6, 1) TB_WR0(8, 1) TB_WR0(10, 1) TB_WR0(12, 1) TB_WR0(14, 1)
-#undef TB_WR0
-    } else {
-        smem_write_run<BOT, R, 0>(P, Q, tile, sb);
-    }
-}
-
-// Barrier of the 256 consumer threads only (named barrier 1); the producer
-// warp never joins it.
-__device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;\n" ::"n"(PASS_CONSUMERS) : "memory"); }
-
-// True on every consumer thread if v is true on any of them.
-__device__ __forceinline__ bool consumer_any(bool v) {
-    uint32_t r;
-    asm volatile(
-        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
-        : "=r"(r)
-        : "r"((uint32_t)v), "n"(PASS_CONSUMERS)
-        : "memory");
-    return r != 0;
-}
-
-// Hand the tile from register run R1 to run R2: every thread writes its
-// entries back to their own slots, then reads the slots of its new run.
-template <bool BOT, int R1, int R2>
-__device__ __forceinline__ void transpose(float2 (&P)[16], float2 (&Q)[16], float2* tile, uint32_t tid) {
-    smem_write<BOT, R1>(P, Q, tile, tid);
-    consumer_sync();
-    smem_read<BOT, R2>(P, Q, tile, tid);
-}
-
-template <class SH, int I, int R>
+template <class SH, int I>
 __device__ __forceinline__ void apply_step(float2 (&P)[16], float2 (&Q)[16], const float2* sc,
                                            uint32_t xmask, float scale, uint32_t tid) {
-    constexpr StepSpec sp = step_spec(SH::TYPE, SH::M, I);
-    constexpr int K = SH::C + sp.t - R;
-    static_assert(K >= 0 && K < REG_BITS, "step target outside its register run");
+    constexpr int T = SH::tgt(I), CB = SH::ctl(I);
     constexpr int kind = step_kind<SH>(I);
-    // control: -1 none, 0..4 run bit, 5 external (a thread bit)
-    constexpr int u = SH::C + sp.c;
-    constexpr int CK = sp.c < 0 ? -1 : (in_run(u, R) ? u - R : 5);
+    // control: -1 none, 0..4 register bit, 5 on a lane (the same for all of
+    // this thread's entries)
+    constexpr int CK = CB < 0 ? -1 : (SH::regpos(CB) >= 0 ? SH::regpos(CB) : 5);
+    const uint32_t lane = tid & 31u;
     const float s = (I == 0) ? scale : 1.0f;
     asm volatile("" ::: "memory");  // load each step's coefficients just before it
     const float2* cf = sc + (I * 2 + (int)((xmask >> I) & 1u)) * CO;
-    float2 c0[12], c1[12];
-    if constexpr (CK == 5) {
-        const uint32_t c = (run_base(R, tid) >> u) & 1u;
-        load_cf(c0, cf + 12 * c, s);
+    if constexpr (kind == KIND_L) {
+        constexpr int L = SH::lanepos(T);
+        static_assert(L >= 0, "lane target");
+        const float2* ca = cf + 24 * ((lane >> L) & 1u);
+        float2 c0[6], c1[6];
+        if constexpr (CK == 5) {
+            load_cf(c0, ca + 6 * ((lane >> SH::lanepos(CB)) & 1u), s);
+        } else if constexpr (CK == 4) {
+            load_cf(c0, ca + 12, s);
+        } else {
+            load_cf(c0, ca, s);
+            if constexpr (CK >= 0) load_cf(c1, ca + 6, s);
+        }
+        step_lane<(CK == 4 || CK == 5) ? -1 : CK>(P, Q, c0, c1, 1 << L);
     } else {
-        load_cf(c0, cf, s);
-    }
-    if constexpr (CK >= 0 && CK < 4) load_cf(c1, cf + 12, s);
-    if constexpr (kind == KIND_VT) {
-        step_lanes<CK>(P, Q, c0, c1);
-    } else {
-        step_pairs<K, (kind == KIND_VC ? 4 : CK)>(P, Q, c0, c1);
+        constexpr int K = SH::regpos(T);
+        float2 c0[12], c1[12];
+        if constexpr (CK == 5) {
+            load_cf(c0, cf + 12 * ((lane >> SH::lanepos(CB)) & 1u), s);
+        } else {
+            load_cf(c0, cf, s);
+        }
+        if constexpr (CK >= 0 && CK < 4) load_cf(c1, cf + 12, s);
+        if constexpr (kind == KIND_VT) {
+            step_halves<(CK == 5) ? -1 : CK>(P, Q, c0, c1);
+        } else {
+            step_pairs<K, (CK == 5) ? -1 : CK>(P, Q, c0, c1);
+        }
     }
 }
 
 template <class SH, int I>
 __device__ __forceinline__ void run_steps(float2 (&P)[16], float2 (&Q)[16], const float2* sc, uint32_t xmask,
-                                          float scale, uint32_t tid, float2* tile) {
+                                          float scale, uint32_t tid) {
     if constexpr (I < SH::NS) {
-        constexpr int R = SH::run_of(I);
-        constexpr int RP = (I == 0) ? SH::first_run() : SH::run_of(I - 1);
-        if constexpr (R != RP) transpose<SH::BOT, RP, R>(P, Q, tile, tid);
-        apply_step<SH, I, R>(P, Q, sc, xmask, scale, tid);
-        run_steps<SH, I + 1>(P, Q, sc, xmask, scale, tid, tile);
+        apply_step<SH, I>(P, Q, sc, xmask, scale, tid);
+        run_steps<SH, I + 1>(P, Q, sc, xmask, scale, tid);
     }
 }
 
@@ -419,10 +408,6 @@ __device__ __forceinline__ int rescale_exp(float m) {
 // ---------------------------------------------------------------------------
 constexpr uint32_t PASS_WAIT_TRIES = 1u << 24;    // far beyond any tile's copy or compute time
 constexpr uint32_t PASS_SELFTEST_TRIES = 1u << 10;
-
-__device__ __forceinline__ uint32_t pass_smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
 
 __device__ __forceinline__ void pbar_init(uint32_t a, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(a), "r"(count) : "memory");
@@ -520,7 +505,7 @@ __global__ void __launch_bounds__(PASS_THREADS, PASS_CTAS_PER_SM)
     if (tid == 0) {
         for (int s = 0; s < PASS_STAGES; ++s) {
             pbar_init(full0 + 8 * s, 1);
-            pbar_init(done0 + 8 * s, PASS_CONSUMERS);
+            pbar_init(done0 + 8 * s, PASS_CONSUMERS / 32);
         }
         *s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -580,7 +565,7 @@ __global__ void __launch_bounds__(PASS_THREADS, PASS_CTAS_PER_SM)
         return;
     }
 
-    // ---------------- consumers (tid < 256)
+    // ---------------- consumers (tid < 256): 8 independent warps
     asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;\n" ::"n"(PASS_CONSUMER_REGS));
     float runmax = 0.0f;
     int64_t cur_b = -1;
@@ -588,12 +573,13 @@ __global__ void __launch_bounds__(PASS_THREADS, PASS_CTAS_PER_SM)
     float scale = 1.0f;
     uint32_t xmask = 0;
     const int64_t tmask = ((int64_t)1 << p.tile_shift) - 1;
+    const uint32_t sb = slot_of<SH::BOT>(thread_base<SH::BOT>(tid));
     int s = 0;
     uint32_t ph = 0;
     for (int64_t k = 0; k < ntl; ++k) {
         const bool gave_up = !pbar_wait(full0 + 8 * s, ph, tries);
-        if (consumer_any(gave_up)) {
-            if (tid == 0 && atomicExch(s_abort, 1) == 0) atomicAdd(p.fault, 1);
+        if (__any_sync(0xffffffffu, gave_up)) {  // the whole warp stops
+            if ((tid & 31u) == 0 && atomicExch(s_abort, 1) == 0) atomicAdd(p.fault, 1);
             break;
         }
         const int64_t gt = first + k * gridDim.x;
@@ -614,14 +600,15 @@ __global__ void __launch_bounds__(PASS_THREADS, PASS_CTAS_PER_SM)
 
         float2* tile = stages + s * TILE;
         float2 P[16], Q[16];
-        smem_read<SH::BOT, SH::first_run()>(P, Q, tile, tid);
-        run_steps<SH, 0>(P, Q, sc, xmask, scale, tid, tile);
+        smem_read_j<SH::BOT, SH::REG0, 0>(P, Q, tile, sb);
+        run_steps<SH, 0>(P, Q, sc, xmask, scale, tid);
 #pragma unroll
         for (int j = 0; j < 16; ++j)
             runmax = fmaxf(runmax, fmaxf(fmaxf(fabsf(P[j].x), fabsf(P[j].y)), fmaxf(fabsf(Q[j].x), fabsf(Q[j].y))));
-        smem_write<SH::BOT, SH::run_of(NS - 1)>(P, Q, tile, tid);
+        smem_write_j<SH::BOT, SH::REG0, 0>(P, Q, tile, sb);
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // visible to the tensor store
-        pbar_arrive(done0 + 8 * s);
+        __syncwarp();
+        if ((tid & 31u) == 0) pbar_arrive(done0 + 8 * s);
         if (++s == PASS_STAGES) { s = 0; ph ^= 1u; }
     }
     if (cur_b >= 0) flush_max(runmax, p.maxs + cur_b * p.sstride + p.slot + 1);
