@@ -145,10 +145,10 @@ def cpu_sample_circuit():
 def cpu_baseline(seconds_cap: float = 30.0, threads: int = 0) -> dict:
     """FP64 oracle (naive row-by-row contraction) on the n=30, d=40 slice with
     the workload's gate statistics, scaled to the n=70, d=64 workload by the
-    ratio of Algorithm 1's contraction costs of the two circuits. threads > 0
-    limits the oracle's OpenMP threads (all host cores otherwise)."""
+    ratio of Algorithm 1's contraction costs of the two circuits, both counted
+    by the oracle itself (no product code is loaded). threads > 0 limits the
+    oracle's OpenMP threads (all host cores otherwise)."""
     import oracle
-    import paper_2608_13110_gb300 as tb
     if threads > 0:
         oracle.set_num_threads(threads)
     c = cpu_sample_circuit()
@@ -162,30 +162,42 @@ def cpu_baseline(seconds_cap: float = 30.0, threads: int = 0) -> dict:
             break
     dt = time.perf_counter() - t0
     slice_rate = done / dt
-    ratio = 2.0 ** (tb.Plan(70, 64).info["log2_cost"] - tb.Plan(*CPU_SAMPLE).info["log2_cost"])
+    ratio = 2.0 ** (oracle.alg1_cost(70, 64)[1] - oracle.alg1_cost(*CPU_SAMPLE)[1])
     return {"value": slice_rate / ratio, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "cpu": _cpu_model(), "sample_amps_per_s": slice_rate,
+            "cpu": _cpu_model(), "sample_amps_per_s": slice_rate, "same_config": False,
             "sample": (f"{done} amplitude(s) of an n={CPU_SAMPLE[0]}, d={CPU_SAMPLE[1]} slice (width 20) "
                        f"in {dt:.1f} s = {slice_rate:.3g} amps/s, divided by the Algorithm 1 cost ratio "
-                       f"C(70,64)/C(30,40) = {ratio:.4g}")}
+                       f"C(70,64)/C(30,40) = {ratio:.4g} (the oracle's own count of the path); the n=70, d=64 "
+                       f"workload itself (2^32-entry FP64 boundary, about 9 h per amplitude) is not run")}
 
 
 # --------------------------------------------------------------------- traffic
+def kernel_code_hash() -> str:
+    """First 16 hex digits of the SHA-256 of the pass kernel's code: the
+    source of pass_kernel.cuh with its comments and all white space removed,
+    so that an edit of a comment keeps the key and any code change breaks it."""
+    import hashlib
+    import re
+    src = open(os.path.join(ROOT, "paper_2608_13110_gb300", "csrc", "pass_kernel.cuh")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    src = re.sub(r"\s+", "", src)
+    return hashlib.sha256(src.encode()).hexdigest()[:16]
+
+
 def pass_traffic(h: int):
     """DRAM bytes per pass launch from the committed ncu summary, scaled to a
     2^h boundary, or None if absent or taken on other kernel sources."""
     path = os.path.join(ROOT, "profiles", "pass_kernel_traffic.txt")
     if not os.path.exists(path):
         return None
-    import hashlib
-    src = os.path.join(ROOT, "paper_2608_13110_gb300", "csrc", "pass_kernel.cuh")
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    digest = kernel_code_hash()
     kv = {}
     for line in open(path):
         if "=" in line and not line.lstrip().startswith("#"):
             k, v = line.split("=", 1)
             kv[k.strip()] = v.strip()
-    if kv.get("pass_kernel_sha256_16") != digest:
+    if kv.get("pass_kernel_code_sha256_16") != digest:
         return None
     try:
         return float(kv["dram_bytes_per_entry"]) * float(2 ** h)
@@ -205,8 +217,11 @@ def run_reference(args, rank, world):
     v = statistics.median(x["value"] for x in vals)
     cb = dict(vals[-1])
     cb["value"] = v
+    # one step of the workload is 16 amplitudes; at the oracle's rate it would take
+    ms = 1e3 * 16 / v
+    cb["ms_per_step_how"] = "16 amplitudes (one workload step) at the oracle's scaled rate"
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
-            "steps": steps, "warmup": warm, "ms_per_step": None, "higher_is_better": True,
+            "steps": steps, "warmup": warm, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "complex128", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": 70, "d": 64, "n_t": 426, "bitstrings_per_step": 16,
                        "parallelism": f"replicas x{world}"},
@@ -227,6 +242,13 @@ def run_ours(args, rank, world, local):
         c = W.random_circuit(n_, d_, None, nb, 4000 + 100 * rank + d_)
     else:
         c = W.precision_70_64(replica=rank, nb=nb)
+    h_ = (c.d + 1) // 2
+    if args.shape:
+        metric = f"amplitudes/s (--shape n={c.n}, d={c.d}, width {h_}; profiling only, not the headline workload)"
+        workload = (f"--shape profiling circuit: brickwork CZ n={c.n} d={c.d}, random Cliffords, {c.n_t} T, "
+                    f"{nb} uniform bitstrings/step, width {h_}")
+    else:
+        metric, workload = METRIC, WORKLOAD
     sched_opts = {}
     if args.precision == "fp32" and not args.default_schedule:
         from paper_2608_13110_gb300 import autotune
@@ -295,10 +317,10 @@ def run_ours(args, rank, world, local):
     traffic = pass_traffic(h) if args.precision == "fp32" else None
 
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_dev_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "complex64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": 70, "d": 64, "n_t": 426, "bitstrings_per_step": nb,
+        "config": {"workload": workload, "n": c.n, "d": c.d, "n_t": int(c.n_t), "bitstrings_per_step": nb,
                    "pass_arithmetic": args.precision,
                    "schedule": ({"autotuned": sched_opts, "tune_s": round(t_tune, 1)} if sched_opts
                                 else "planner default"),
@@ -321,9 +343,9 @@ def run_ours(args, rank, world, local):
                      "pass_share_of_kernel_time": p["ms"] / max(1e-9, sum(v["ms"] for v in prof.values())),
                      "fma_pipe": fma_pipe_fraction(args, info, nb, h, p, clk, dev)},
         "clocks": clk,
-        "sanity": {"log_xeb": tb.log_xeb(amps, 70), "e2e_matches_device": bool(np.array_equal(amps, e2e_amps))},
+        "sanity": {"log_xeb": tb.log_xeb(amps, c.n), "e2e_matches_device": bool(np.array_equal(amps, e2e_amps))},
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.shape:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, args.cpu_threads)
         line["cpu_baseline"]["gpu_same_sample"] = gpu_rate_on_cpu_sample(tb, dev, stream, line["cpu_baseline"])
     if rank == 0:

@@ -376,6 +376,21 @@ TB_API int tb_amplitudes_noalloc(const tb_plan* plan, const uint8_t* d_bits, int
  * A zero amplitude gives -inf. */
 TB_API int tb_log_xeb(const double* amp, int64_t nb, int n, double* out);
 
+/* The same estimator on the device, in FP64 (Sec. 5.2, normalized log-XEB
+ * equation; the final reduction of the sweep's amplitudes stays on the GPU).
+ *   d_amp : device, 2*nb doubles (re, im), e.g. the d_out of
+ *           tb_amplitudes_device; read only.
+ *   nb    : number of amplitudes, >= 1.
+ *   n     : number of qubits (the n ln 2 term).
+ *   d_out : device, one double; receives F.
+ *   stream: cudaStream_t (NULL: legacy default stream). The reduction is
+ *           enqueued after the work already on the stream and the call returns
+ *           without synchronising.
+ * One CTA sums ln |amp|^2 in a fixed order (deterministic); a zero amplitude
+ * gives -inf. Returns TB_OK, TB_EINVAL (NULL pointer, nb < 1, n < 1) or
+ * TB_ECUDA (launch failure). */
+TB_API int tb_log_xeb_device(const double* d_amp, int64_t nb, int n, double* d_out, void* stream);
+
 /* The Clifford table this library uses: m receives C_k as in tb_gate1q. */
 TB_API int tb_clifford_matrix(int k, double m[8]);
 

@@ -20,7 +20,10 @@ ways:
   Aaronson-Gottesman stabilizer tableau (C);
 * ``closed_form_hdiag`` -- closed form for circuits whose first and last slots
   are H on every qubit and whose interior slots are diagonal (numpy);
-* ``log_xeb`` -- the log-XEB estimator of Sec. 5.2 (numpy).
+* ``log_xeb`` -- the log-XEB estimator of Sec. 5.2 (numpy);
+* ``alg1_cost`` -- contraction width W and cost log2 C of Algorithm 1's path
+  (Sec. 2.2 cost definitions, Sec. 3.1), counted over the network's legs
+  (pure Python).
 
 Readings of points the paper leaves open (also listed in the design notes):
 d+1 one-qubit slots, slot t < d before CZ layer t; U_(q,t) = T^tau . C (the
@@ -29,7 +32,8 @@ C_k = P_(k mod 4) . R_(k div 4) with P in (I, X, Y, Z), Y = [[0,-i],[i,0]],
 R in (I, H, S, S.H, H.S, H.S.H); layer l couples (i, i+1) for i = l (mod 2).
 
 Pins: see tests/test_oracle_pins.py (brute force, Kronecker product, norm,
-tableau, closed form, identity circuit). Every function here is pinned.
+tableau, closed form, identity circuit, the paper's printed (W, log2 C) and
+Proposition 1's width). Every function here is pinned.
 """
 from __future__ import annotations
 
@@ -318,3 +322,68 @@ def rel_l2(a: np.ndarray, ref: np.ndarray) -> float:
 if __name__ == "__main__":  # pragma: no cover
     build(force="--force" in sys.argv)
     print(_LIB_PATH)
+
+
+def alg1_cost(n: int, d: int) -> tuple:
+    """(W, log2 C) of the constructive path of Algorithm 1 (Sec. 3.1) for the
+    amplitude network of an n-qubit, depth-d brickwork circuit (Sec. 2.2).
+
+    The network (Sec. 2.2): every CZ is split into two rank-3 halves, one per
+    qubit, joined by a bond of dimension chi = 2; the halves of one qubit are
+    chained in time by legs of dimension 2; the input state, the output
+    projector and the one-qubit gates are absorbed, so the first and last
+    half of a qubit carry one time leg. Every leg has dimension 2, so a
+    tensor's log2 size is its number of legs.
+
+    The path: the halves in FixedSweepOrder -- qubit rows 0..n-1, row 0 and
+    odd rows in forward time, even rows >= 2 in reversed time (the paper's
+    "reverse time on even-numbered rows" under the layer convention that
+    layer l couples (i, i+1) for i = l mod 2). The boundary B starts as the
+    first tensor; the next tensor X is contracted into B if the result has at
+    most h = ceil(d/2) legs, otherwise X is first contracted with the tensor
+    after it and the pair is contracted into B. A pairwise contraction of
+    A_IK B_KJ costs |I||J||K| = 2^(#legs of A union B) (Sec. 2.2); W is the
+    largest log2 size of any tensor the path creates."""
+    h = (d + 1) // 2
+    rows = []
+    for q in range(n):
+        layers = [l for l in range(d)
+                  if (l % 2 == q % 2 and q + 1 < n) or (q >= 1 and l % 2 == (q - 1) % 2)]
+        legs = []
+        for i, l in enumerate(layers):
+            lo = q if l % 2 == q % 2 else q - 1          # the bond's upper qubit is lo + 1
+            t = {("bond", l, lo)}
+            if i > 0:
+                t.add(("time", q, i - 1))
+            if i + 1 < len(layers):
+                t.add(("time", q, i))
+            legs.append(frozenset(t))
+        if q >= 2 and q % 2 == 0:
+            legs.reverse()
+        rows.append(legs)
+    order = [t for r in rows for t in r]
+    if not order:
+        return 0, float("-inf")
+    costs = []
+    width = 0
+    B = set(order[0])
+    width = max(width, len(B))
+    i = 1
+    while i < len(order):
+        X = order[i]
+        if len(B ^ X) <= h:
+            costs.append(len(B | X))
+            B = B ^ X
+            i += 1
+        else:
+            Y = order[i + 1]
+            costs.append(len(X | Y))
+            Cxy = X ^ Y
+            width = max(width, len(Cxy))
+            costs.append(len(B | Cxy))
+            B = B ^ Cxy
+            i += 2
+        width = max(width, len(B))
+    m = max(costs)
+    log2c = m + float(np.log2(sum(2.0 ** (c - m) for c in costs)))
+    return width, log2c

@@ -69,6 +69,7 @@ _sig = {
     "tb_profile_begin": (ctypes.c_int, []),
     "tb_profile_end": (ctypes.c_int, [ctypes.c_void_p]),
     "tb_log_xeb": (ctypes.c_int, [_dp, ctypes.c_int64, ctypes.c_int, _dp]),
+    "tb_log_xeb_device": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int, _vp, _vp]),
     "tb_clifford_matrix": (ctypes.c_int, [ctypes.c_int, _dp]),
     "tb_plan_destroy": (None, [_vp]),
     "tb_status_str": (ctypes.c_char_p, [ctypes.c_int]),
@@ -481,6 +482,19 @@ def log_xeb(amps, n: int) -> float:
     out = ctypes.c_double(0.0)
     _check(_lib.tb_log_xeb(a.ctypes.data_as(_dp), a.size // 2, int(n), ctypes.byref(out)), "tb_log_xeb")
     return float(out.value)
+
+
+def log_xeb_device(d_amps, n: int, d_out, stream=None) -> None:
+    """Enqueue the FP64 log-XEB reduction of device amplitudes ``d_amps``
+    (torch float64 tensor of shape (nb, 2), e.g. the output of
+    ``Plan.amplitudes_device``) into ``d_out`` (torch float64 tensor, one
+    element) on ``stream`` (default: the current stream). No synchronisation."""
+    import torch
+    if d_amps.dtype != torch.float64 or d_out.dtype != torch.float64 or not d_amps.is_contiguous():
+        raise TypeError("d_amps and d_out must be contiguous float64 device tensors")
+    st = stream if stream is not None else torch.cuda.current_stream(d_amps.device)
+    _check(_lib.tb_log_xeb_device(d_amps.data_ptr(), d_amps.numel() // 2, int(n), d_out.data_ptr(),
+                                  st.cuda_stream), "tb_log_xeb_device")
 
 
 def clifford_matrix(k: int) -> np.ndarray:

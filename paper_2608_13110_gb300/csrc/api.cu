@@ -715,6 +715,13 @@ int tb_log_xeb(const double* amp, int64_t nb, int n, double* out) {
     return TB_OK;
 }
 
+int tb_log_xeb_device(const double* d_amp, int64_t nb, int n, double* d_out, void* stream) {
+    if (!d_amp || !d_out || nb <= 0 || n < 1) return fail(TB_EINVAL, "bad argument");
+    TB_CUDA(launch_log_xeb(reinterpret_cast<const double2*>(d_amp), nb, n, d_out,
+                           static_cast<cudaStream_t>(stream)));
+    return TB_OK;
+}
+
 int tb_clifford_matrix(int k, double m[8]) {
     if (k < 0 || k > 23 || !m) return fail(TB_EINVAL, "index must be 0..23");
     const M2 c = clifford(k);

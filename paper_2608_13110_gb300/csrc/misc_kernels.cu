@@ -173,6 +173,37 @@ __global__ void finalize_kernel(const FinalizeParams p) {
     }
 }
 
+// ---- log-XEB (Sec. 5.2, normalized log-XEB estimator) -----------------------
+// F = gamma + n ln 2 + (1/N) sum_i ln |amp_i|^2, entirely in FP64 on the
+// device. One CTA: thread t sums the terms i = t, t + 1024, ... in index
+// order, then a fixed binary tree adds the 1024 partial sums, so the result
+// does not depend on scheduling. A zero amplitude contributes -inf.
+constexpr int XEB_THREADS = 1024;
+
+__global__ void __launch_bounds__(XEB_THREADS) log_xeb_kernel(const double2* amp, int64_t nb, int n, double* out) {
+    __shared__ double part[XEB_THREADS];
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < nb; i += XEB_THREADS) {
+        const double2 a = amp[i];
+        s += log(fma(a.x, a.x, a.y * a.y));
+    }
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = XEB_THREADS / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double gamma = 0.57721566490153286060651209;  // Euler's constant
+        out[0] = gamma + (double)n * 0.69314718055994530941723212 + part[0] / (double)nb;
+    }
+}
+
+cudaError_t launch_log_xeb(const double2* amp, int64_t nb, int n, double* out, cudaStream_t st) {
+    log_xeb_kernel<<<1, XEB_THREADS, 0, st>>>(amp, nb, n, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_finalize(const FinalizeParams& p, cudaStream_t st) {
     const int warps = 4;
     finalize_kernel<<<(p.nbatch + warps - 1) / warps, 32 * warps, 0, st>>>(p);

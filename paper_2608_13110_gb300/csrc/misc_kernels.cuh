@@ -78,6 +78,8 @@ constexpr int MAX_RED_BLOCKS = 1024;
 cudaError_t launch_init(const InitParams& p, int grid, cudaStream_t st);
 cudaError_t launch_reduce(const ReduceParams& p, cudaStream_t st);
 cudaError_t launch_finalize(const FinalizeParams& p, cudaStream_t st);
+// log-XEB estimator of nb device amplitudes (FP64, one CTA, fixed order).
+cudaError_t launch_log_xeb(const double2* amp, int64_t nb, int n, double* out, cudaStream_t st);
 cudaError_t launch_small(const SmallParams& p, cudaStream_t st);
 cudaError_t launch_small_multi(const SmallItem* d_items, int nitems, int64_t nblocks, int hmax, cudaStream_t st);
 

@@ -46,6 +46,15 @@ def test_width_and_cost_at_n70_d70(tb):
     assert abs(info["log2_cost"] - g["log2_C"]) < g["log2_C_tolerance"]
 
 
+def test_planner_counters_equal_the_oracle_count(tb, oracle_mod):
+    """The planner's W and log2 C (which the benchmark's CPU baseline does not
+    use) agree with the oracle's independent count of Algorithm 1's path."""
+    for n, d in [(70, 70), (70, 64), (30, 40), (70, 56), (32, 48), (12, 8), (70, 63), (5, 9), (13, 25)]:
+        info = tb.Plan(n, d).info
+        w, c = oracle_mod.alg1_cost(n, d)
+        assert info["width"] == w and abs(info["log2_cost"] - c) < 1e-9, (n, d)
+
+
 def test_constructive_width_is_ceil_d_over_2(tb):
     g = GOLDEN["constructive_width"]
     for d in g["d"]:
@@ -341,6 +350,10 @@ def test_null_and_out_of_range_arguments_fail_without_device_work(tb):
     amps = np.ones(4, np.float64)
     assert L.tb_log_xeb(None, 2, 10, ctypes.byref(out)) == tb.TB_EINVAL
     assert L.tb_log_xeb(amps.ctypes.data_as(tb._dp), 0, 10, ctypes.byref(out)) == tb.TB_EINVAL
+    # the device reduction checks its arguments before any device work
+    assert L.tb_log_xeb_device(None, 2, 10, None, None) == tb.TB_EINVAL
+    assert L.tb_log_xeb_device(ctypes.c_void_p(16), 0, 10, ctypes.c_void_p(16), None) == tb.TB_EINVAL
+    assert L.tb_log_xeb_device(ctypes.c_void_p(16), 2, 0, ctypes.c_void_p(16), None) == tb.TB_EINVAL
     assert L.tb_plan_create(8, 10, None, None, None, 0, None, None) == tb.TB_EINVAL
     h = tb._vp()
     assert L.tb_plan_create(8, 10, None, None, None, -1, None, ctypes.byref(h)) == tb.TB_EINVAL

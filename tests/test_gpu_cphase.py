@@ -54,8 +54,8 @@ def test_narrow_random_unitaries_and_phases(tb, oracle_mod, n, d):
     assert rel_l2(plan.amplitudes(bits), oracle_mod.sv_amplitudes(n, d, u, bits, ph)) < TOL
 
 
-@pytest.mark.parametrize("n,d,wb,bb,tt", [(6, 42, 6, 8, 5), (6, 44, 10, 7, 7), (7, 26, 5, 9, 5),
-                                          (7, 28, 5, 5, 10), (6, 41, 6, 8, 5), (16, 40, 0, 0, 0),
+@pytest.mark.parametrize("n,d,wb,bb,tt", [(6, 42, 6, 8, 5), (6, 44, 9, 8, 7), (7, 26, 5, 9, 5),
+                                          (7, 26, 5, 6, 8), (6, 41, 6, 8, 5), (16, 40, 0, 0, 0),
                                           (17, 45, 0, 0, 0)])
 def test_pass_schedule_vs_state_vector(tb, oracle_mod, n, d, wb, bb, tt):
     c = W.random_circuit(n, d, None, 48, 9900 + 31 * n + d)

@@ -362,3 +362,41 @@ def test_log_xeb_definition(oracle_mod):
     amps = np.sqrt(z / 2.0 ** n).astype(np.complex128)
     sd = np.pi / np.sqrt(6.0) / np.sqrt(N)
     assert abs(oracle_mod.log_xeb(amps, n)) < 5 * sd
+
+
+# ------------------------------------------------- Algorithm 1 cost counter
+
+def _paper_numbers():
+    import json
+    import os
+    return json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_numbers.json")))
+
+
+def test_alg1_cost_matches_the_paper_at_n70_d70(oracle_mod):
+    """Sec. 6.2 / 6.3 print (W, log2 C) = (35, 48.22) for the chi=2 open chain
+    at n = d = 70. A wrong sweep direction, a dropped bond or time leg, or a
+    cost other than |I||J||K| moves one of the two numbers."""
+    g = _paper_numbers()["width_cost_open_chi2_n70_d70"]
+    w, c = oracle_mod.alg1_cost(g["n"], g["d"])
+    assert w == g["W"]
+    assert abs(c - g["log2_C"]) < g["log2_C_tolerance"]
+
+
+def test_alg1_width_is_proposition_1(oracle_mod):
+    """Proposition 1: the constructive path has width ceil(d/2) for n >= 4 and
+    7 <= d <= 2n (the values listed in the paper for n = 70, and a spread of
+    smaller even and odd cases)."""
+    g = _paper_numbers()["constructive_width"]
+    for d in g["d"]:
+        assert oracle_mod.alg1_cost(g["n"], d)[0] == (d + 1) // 2, d
+    for n, d in [(4, 7), (5, 9), (8, 16), (12, 9), (20, 33), (30, 40), (33, 66)]:
+        assert oracle_mod.alg1_cost(n, d)[0] == (d + 1) // 2, (n, d)
+
+
+def test_alg1_cost_brute_force_on_a_tiny_network(oracle_mod):
+    """n = 2, d = 2: two qubits, one CZ in layer 0 only (layer 1 couples (1, 2),
+    which does not exist). Each qubit has one half with only the bond leg:
+    B = {bond} (1 leg), X = {bond}: one contraction of two 1-leg tensors over
+    the shared bond, |I||J||K| = 1 * 1 * 2 = 2, so log2 C = 1 and W = 1."""
+    w, c = oracle_mod.alg1_cost(2, 2)
+    assert w == 1 and abs(c - 1.0) < 1e-12
