@@ -250,7 +250,11 @@ def run_ours(args, rank, world, local):
     else:
         metric, workload = METRIC, WORKLOAD
     sched_opts = {}
-    if args.precision == "fp32" and not args.default_schedule:
+    t_tune = 0.0
+    if args.schedule:
+        wb, bb, tt = (int(v) for v in args.schedule.split(","))
+        sched_opts = {"window_bits": wb, "bottom_bits": bb, "top_bits": tt}
+    elif args.precision == "fp32" and not args.default_schedule:
         from paper_2608_13110_gb300 import autotune
         t_tune = time.perf_counter()
         sched_opts = autotune.tune((c.d + 1) // 2, nb)
@@ -322,8 +326,9 @@ def run_ours(args, rank, world, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "complex64", "data": "synthetic",
         "config": {"workload": workload, "n": c.n, "d": c.d, "n_t": int(c.n_t), "bitstrings_per_step": nb,
                    "pass_arithmetic": args.precision,
-                   "schedule": ({"autotuned": sched_opts, "tune_s": round(t_tune, 1)} if sched_opts
-                                else "planner default"),
+                   "schedule": ({"given": sched_opts} if args.schedule else
+                                ({"autotuned": sched_opts, "tune_s": round(t_tune, 1)} if sched_opts
+                                 else "planner default")),
                    "width": info["width"], "passes_per_amplitude": info["n_passes"],
                    "l2": "inputs larger than L2 (32 GiB boundary, 129 MB L2)",
                    "parallelism": f"replicas x{world}"},
@@ -762,6 +767,8 @@ def main():
                     help="pass arithmetic of the n70d64 workload")
     ap.add_argument("--default-schedule", action="store_true",
                     help="use the planner's default window schedule instead of the autotuned one")
+    ap.add_argument("--schedule", default="",
+                    help="window_bits,bottom_bits,top_bits of the n70d64 workload (no autotuning; profiling)")
     ap.add_argument("--nb-precision", type=int, default=4, help="bitstrings per step in the precision workload")
     ap.add_argument("--requests", type=int, default=200, help="requests in the serve workload")
     ap.add_argument("--serve-slots", type=int, default=2,
