@@ -355,9 +355,10 @@ TB_API int tb_profile_end(tb_profile_t* out);
  * rescaling state and boundary live in a fixed 64 MiB scratch array compiled
  * into this library, so the call needs no workspace and calls no cudaMalloc.
  * The paper has no counterpart; this entry exists for callers that cannot
- * allocate device memory at the point of use (work recorded into a CUDA graph,
- * processes under a device-memory quota owned by someone else, plugins that
- * must not create untracked allocations).
+ * allocate device memory at the point of use: processes whose device memory is
+ * capped by a quota someone else owns, and plugins or libraries embedded in a
+ * host application that tracks every device allocation and must not see
+ * untracked ones.
  *   d_bits: device, nb*n bytes; d_out: device, 2*nb doubles (re, im).
  * Limits and behaviour:
  *   - plans whose tables plus one boundary exceed 64 MiB (for n = 70: width

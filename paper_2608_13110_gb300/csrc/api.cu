@@ -425,12 +425,11 @@ using namespace tb;
 using namespace tb::rt;
 
 // ---- evaluation without device allocation ----------------------------------
-// Some callers cannot call cudaMalloc when they need amplitudes: code that
-// records work into a CUDA graph (allocation is not a capturable operation),
-// a process that runs under a device-memory quota fixed by someone else, or a
-// plugin that must not create allocations the host application does not
-// track. For them the library carries one fixed scratch area in device memory,
-// a file-scope array that every GPU loading the library holds until exit.
+// Some callers cannot call cudaMalloc when they need amplitudes: a process
+// whose device memory is capped by a quota someone else owns, or a plugin
+// inside a host application that tracks every device allocation. For them the
+// library carries one fixed scratch area in device memory, a file-scope array
+// that every GPU loading the library holds until exit.
 namespace {
 constexpr int64_t NOALLOC_SCRATCH_BYTES = (int64_t)64 << 20;  // 64 MiB per device
 static __device__ __align__(256) uint8_t g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];

@@ -1,9 +1,10 @@
 """The allocation-free entry point (tb_amplitudes_noalloc) against the
 workspace entry point (tb_amplitudes_device), through the C-ABI.
 
-Callers that cannot allocate device memory when they need amplitudes (work
-recorded into a CUDA graph, processes under someone else's memory quota)
-use the library's fixed scratch array instead of a workspace. Its results
+Callers that cannot allocate device memory when they need amplitudes (a
+process whose device memory is capped by someone else's quota, a plugin whose
+host application tracks every device allocation) use the library's fixed
+scratch array instead of a workspace. Its results
 must match the workspace path on consecutive calls, since every call reuses
 whatever the previous one left in that array. This file is collected last so
 that a run stopping at the first failure has already run every other test.
