@@ -49,7 +49,7 @@ enum tb_status {
                         ceil(d/2) > 40 for a plan, > 33 for evaluation */
     TB_ENOMEM = 3,   /* workspace smaller than tb_workspace_bytes() or host allocation failed */
     TB_ECUDA = 4,    /* a CUDA runtime call failed; tb_last_error() has the message */
-    TB_ETIMEOUT = 5  /* reserved for bounded device waits */
+    TB_ETIMEOUT = 5  /* a bounded device wait gave up, or a server wait timed out */
 };
 
 /* Opaque plan: the folded gates, the step tables and the pass schedule of one
@@ -321,7 +321,10 @@ TB_API int tb_server_submit(tb_server* server, const tb_plan* plan, const uint8_
                             double* out, int64_t* ticket);
 
 /* Wait for a request (timeout_s < 0: no limit; TB_ETIMEOUT when it runs out,
- * and the ticket stays valid). Returns the request's status; fills stats. */
+ * stats untouched and the ticket still valid). Once the request has finished,
+ * returns its status (TB_ETIMEOUT there means a bounded device wait of its
+ * kernels gave up and out is not written; stats->status says the same) and
+ * consumes the ticket; fills stats. */
 TB_API int tb_server_wait(tb_server* server, int64_t ticket, double timeout_s, tb_request_stats* stats);
 
 /* Counters and latency percentiles of completed requests. */
@@ -405,24 +408,37 @@ TB_API const char* tb_status_str(int status);
 TB_API const char* tb_last_error(void);
 
 /* Device-side wait failures (no counterpart in the paper). Every spin-wait in
- * the library's kernels (the tensor-core passes wait for their MMAs to
- * complete) gives up after a bounded number of tries; a kernel that gives up
- * counts it in a device word, leaves its results undefined and exits cleanly
- * (its tensor memory released), so the context stays usable.
+ * the library's kernels (the FP32 passes wait for their tile copies and for
+ * their consumer warps, the tensor-core passes for their MMAs) gives up after
+ * a bounded number of tries; a kernel that gives up counts it in a fault word,
+ * writes nothing more for the affected tiles (the amplitudes of that call are
+ * not valid) and exits cleanly, so the context stays usable.
+ *   - tb_amplitudes and server requests use a fault word of their own and
+ *     return TB_ETIMEOUT when it is nonzero;
+ *   - tb_amplitudes_device, tb_amplitudes_noalloc and batches are
+ *     asynchronous: their kernels count in the library-wide word, which the
+ *     caller reads here after synchronising.
+ * A tensor-core pass that cannot confirm that its last MMAs completed keeps
+ * its tensor memory rather than free it under a running MMA; after that the
+ * library refuses further split-precision evaluations in this process
+ * (TB_ECUDA).
  * *count receives the number of failed waits since the last call on the
  * current device, and the word is cleared. Synchronises the device.
  * Returns TB_OK, TB_EINVAL (NULL count) or TB_ECUDA. */
 TB_API int tb_device_faults(int32_t* count);
 
-/* Self-test of the bounded device waits (no counterpart in the paper): one
- * small split-precision evaluation (n = 3, d = 26, 3xBF16) whose tensor-core
- * kernels wait for MMAs that are never issued. Each wait gives up after a
- * short bounded number of tries and is counted; the kernels stop, release
- * their tensor memory and exit, so the device stays usable (nothing faults or
- * hangs). *faults receives the number of waits that gave up (positive when the
- * mechanism works); the result of that evaluation is discarded. Allocates and
- * frees a small workspace; synchronises the device. Returns TB_OK, TB_EINVAL
- * (NULL faults) or TB_ECUDA. */
+/* Self-test of the bounded device waits (no counterpart in the paper), with
+ * no fault of any kind: (1) one small split-precision evaluation (n = 3,
+ * d = 26, 3xBF16, asynchronous entry) whose tensor-core kernels wait for MMAs
+ * that are never issued; (2) one FP32 evaluation of the same size through
+ * tb_amplitudes whose pass kernels wait for tile copies that are never issued
+ * and must return TB_ETIMEOUT. Each wait gives up after a short bounded number
+ * of tries and is counted; the kernels stop and exit, so the device stays
+ * usable. *faults receives the number of CTAs whose waits gave up in both
+ * parts (positive when the mechanism works); the results are discarded.
+ * Allocates and frees small workspaces; synchronises the device. Returns
+ * TB_OK, TB_EINVAL (NULL faults) or TB_ECUDA (including: the synchronous entry
+ * did not report the give-up). */
 TB_API int tb_selftest_bounded_wait(int32_t* faults);
 
 #ifdef __cplusplus

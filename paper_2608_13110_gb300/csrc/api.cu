@@ -81,6 +81,8 @@ bool small_path(const Plan& P) { return P.h <= SMALL_H_MAX; }
 // Set by tb_selftest_bounded_wait for the evaluation it runs on this thread.
 thread_local bool t_tc_selftest = false;
 thread_local bool t_pass_selftest = false;
+// Waits that gave up in this thread's last tb_amplitudes call.
+thread_local int t_last_faults = 0;
 
 CallLayout call_layout(const Plan& P) {
     CallLayout c;
@@ -97,7 +99,7 @@ CallLayout call_layout(const Plan& P) {
 }
 
 int64_t staging_bytes(const Plan& P, int64_t nb) {
-    return align_up(nb * in_row(P), 256) + align_up(nb * 16 * amps_per_row(P), 256);
+    return align_up(nb * in_row(P), 256) + align_up(nb * 16 * amps_per_row(P), 256) + 256;  // + fault word
 }
 
 int64_t max_batch(const Plan& P, const CallLayout& c) {
@@ -210,8 +212,12 @@ const T* tab(const void* ws, int64_t off) {
 
 // Enqueue the sweep for nb bitstrings already on the device.
 int run_device(const Plan& P, const uint8_t* d_bits, int64_t nb, void* d_ws, int64_t ws_bytes,
-               int64_t region_off, double* d_out, cudaStream_t st) {
+               int64_t region_off, double* d_out, cudaStream_t st, int* fault) {
     const TableLayout& L = P.lay;
+    if (!fault && !small_path(P)) {
+        fault = device_fault_word();
+        if (!fault) return fail(TB_ECUDA, "device fault word not found");
+    }
     if (small_path(P)) {
         SmallParams sp;
         sp.n = P.n;
@@ -278,8 +284,9 @@ int run_device(const Plan& P, const uint8_t* d_bits, int64_t nb, void* d_ws, int
         }
 
         if (P.opts.precision != TB_PRECISION_FP32) {
-            int* fault = device_fault_word();
-            if (!fault) return fail(TB_ECUDA, "device fault word not found");
+            if (tc_passes_disabled())
+                return fail(TB_ECUDA, "tensor-core passes are disabled in this process: a pass could not confirm "
+                                      "that its MMAs completed and kept its tensor memory");
             const uint8_t* mats = static_cast<const uint8_t*>(d_ws) + L.tc_mats;
             for (size_t k = 0; k < P.tc_passes.size(); ++k) {
                 const TcPass& d = P.tc_passes[k];
@@ -305,8 +312,6 @@ int run_device(const Plan& P, const uint8_t* d_bits, int64_t nb, void* d_ws, int
                 TB_CUDA(launch_tc_pass(P.opts.precision, tp, grid, st));
             }
         }
-        int* fault = P.passes.empty() ? nullptr : device_fault_word();
-        if (!P.passes.empty() && !fault) return fail(TB_ECUDA, "device fault word not found");
         for (size_t k = 0; k < P.passes.size(); ++k) {
             const PassDesc& d = P.passes[k];
             PassParams pp;
@@ -592,12 +597,21 @@ int tb_amplitudes(const tb_plan* plan, const uint8_t* bits, int64_t nb, void* d_
     uint8_t* ws = static_cast<uint8_t*>(d_ws);
     uint8_t* d_bits = ws + P.lay.total;
     double* d_out = reinterpret_cast<double*>(ws + P.lay.total + align_up(nb * in_row(P), 256));
+    int* d_fault = reinterpret_cast<int*>(ws + P.lay.total + stage - 256);
     TB_CUDA(cudaMemcpyAsync(d_ws, P.blob.data(), (size_t)P.lay.total, cudaMemcpyHostToDevice, st));
     TB_CUDA(cudaMemcpyAsync(d_bits, bits, (size_t)(nb * in_row(P)), cudaMemcpyHostToDevice, st));
-    const int rc = run_device(P, d_bits, nb, d_ws, ws_bytes, P.lay.total + stage, d_out, st);
+    TB_CUDA(cudaMemsetAsync(d_fault, 0, sizeof(int), st));
+    const int rc = run_device(P, d_bits, nb, d_ws, ws_bytes, P.lay.total + stage, d_out, st, d_fault);
     if (rc != TB_OK) return rc;
     TB_CUDA(cudaMemcpyAsync(out, d_out, (size_t)(16 * nb * amps_per_row(P)), cudaMemcpyDeviceToHost, st));
+    int faults = 0;
+    TB_CUDA(cudaMemcpyAsync(&faults, d_fault, sizeof(int), cudaMemcpyDeviceToHost, st));
     TB_CUDA(cudaStreamSynchronize(st));
+    faults = note_faults(faults);
+    t_last_faults = faults;
+    if (faults != 0)
+        return fail(TB_ETIMEOUT, "a bounded device wait gave up in " + std::to_string(faults) +
+                                     " CTA(s); the amplitudes are not valid");
     return TB_OK;
 }
 
@@ -656,6 +670,29 @@ int tb_selftest_bounded_wait(int32_t* faults) {
     cudaFree(out);
     cudaFree(ws);
     tb_plan_destroy(plan);
+    if (rc != TB_OK) return rc;
+    // the FP32 pass kernels through the synchronous entry: their producer
+    // issues no tile copies, every wait gives up, and tb_amplitudes must say so
+    plan = nullptr;
+    rc = tb_plan_create(3, 26, nullptr, nullptr, nullptr, 0, nullptr, &plan);
+    if (rc != TB_OK) return rc;
+    const int64_t wsb2 = tb_workspace_bytes(plan, 1);
+    void* ws2 = nullptr;
+    if (cudaMalloc(&ws2, (size_t)wsb2) != cudaSuccess) rc = fail(TB_ECUDA, "self-test allocation failed");
+    if (rc == TB_OK) {
+        const uint8_t hbits[3] = {0, 0, 0};
+        double hout[2] = {0.0, 0.0};
+        t_pass_selftest = true;
+        const int r2 = tb_amplitudes(plan, hbits, 1, ws2, wsb2, hout, nullptr);
+        t_pass_selftest = false;
+        if (r2 != TB_ETIMEOUT)
+            rc = fail(TB_ECUDA, "self-test: the pass kernels' bounded waits were not reported (status " +
+                                    std::to_string(r2) + ")");
+        else
+            *faults += t_last_faults;
+    }
+    cudaFree(ws2);
+    tb_plan_destroy(plan);
     return rc;
 }
 
@@ -667,7 +704,7 @@ int tb_device_faults(int32_t* count) {
     int v = 0;
     TB_CUDA(cudaMemcpy(&v, w, sizeof(int), cudaMemcpyDeviceToHost));
     TB_CUDA(cudaMemset(w, 0, sizeof(int)));
-    *count = v;
+    *count = note_faults(v);
     return TB_OK;
 }
 

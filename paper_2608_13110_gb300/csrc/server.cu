@@ -28,6 +28,7 @@
 
 #include "tb_plan.h"
 #include "tb_run.h"
+#include "tc_pass.cuh"
 #include "tbsweep.h"
 
 using namespace tb;
@@ -145,7 +146,9 @@ namespace {
 
 // Bytes a request needs beyond its plan's tables: staged bitstrings and
 // amplitudes plus k boundaries (per_b each).
-int64_t staging_len(const Plan& P, int64_t nb) { return align_up(nb * P.n, 256) + align_up(16 * nb, 256); }
+// The last 256 bytes hold the request's fault word (bounded device waits
+// that gave up), copied back with the amplitudes.
+int64_t staging_len(const Plan& P, int64_t nb) { return align_up(nb * P.n, 256) + align_up(16 * nb, 256) + 256; }
 
 void release_request(tb_server* S, Request& R) {
     if (R.region_off >= 0) S->arena.release(R.region_off);
@@ -164,6 +167,13 @@ void finish(tb_server* S, int k) {
     if (R->status == TB_OK) {
         const cudaError_t e = cudaEventQuery(S->slot_done[k]);
         if (e != cudaSuccess) R->status = fail(TB_ECUDA, std::string("request failed: ") + cudaGetErrorString(e));
+    }
+    if (R->status == TB_OK) {
+        int faults = 0;
+        std::memcpy(&faults, S->pinned + R->stage_off + staging_len(R->plan->p, R->nb) - 256, sizeof(int));
+        faults = note_faults(faults);
+        if (faults != 0)
+            R->status = fail(TB_ETIMEOUT, "a bounded device wait gave up; the amplitudes are not valid");
     }
     if (R->status == TB_OK)
         std::memcpy(R->out, S->pinned + R->stage_off + align_up(R->nb * R->plan->p.n, 256), (size_t)(16 * R->nb));
@@ -253,14 +263,18 @@ bool admit(tb_server* S, const std::shared_ptr<Request>& Rp, int k) {
     int rc = TB_OK;
     if (cudaMemcpyAsync(d_bits, h_bits, R.bits.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
         rc = fail(TB_ECUDA, "bitstring upload failed");
+    int* d_fault = reinterpret_cast<int*>(arena + reg + st_len - 256);
+    if (rc == TB_OK && cudaMemsetAsync(d_fault, 0, sizeof(int), st) != cudaSuccess)
+        rc = fail(TB_ECUDA, "fault word reset failed");
     if (rc == TB_OK) {
         uint8_t* tab = arena + te.off;
         const int64_t region_off = (reg + st_len) - te.off;
-        rc = run_device(P, d_bits, R.nb, tab, region_off + kb * c.per_b, region_off, d_out, st);
+        rc = run_device(P, d_bits, R.nb, tab, region_off + kb * c.per_b, region_off, d_out, st, d_fault);
     }
     if (rc == TB_OK &&
-        cudaMemcpyAsync(h_bits + align_up(R.nb * P.n, 256), d_out, (size_t)(16 * R.nb), cudaMemcpyDeviceToHost, st) !=
-            cudaSuccess)
+        (cudaMemcpyAsync(h_bits + align_up(R.nb * P.n, 256), d_out, (size_t)(16 * R.nb), cudaMemcpyDeviceToHost,
+                         st) != cudaSuccess ||
+         cudaMemcpyAsync(h_bits + st_len - 256, d_fault, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess))
         rc = fail(TB_ECUDA, "amplitude download failed");
     if (cudaEventRecord(S->slot_done[k], st) != cudaSuccess && rc == TB_OK) rc = fail(TB_ECUDA, "event record failed");
     R.status = rc;

@@ -44,8 +44,10 @@ int num_sms();
 // Enqueue the sweep for nb device-resident bitstrings on stream st; the
 // plan's tables are at the head of d_ws, the per-bitstring region starts at
 // region_off. Returns a tb_status.
+// fault: device int that kernels whose bounded waits give up increment (NULL:
+// the library-wide word read by tb_device_faults).
 int run_device(const Plan& P, const uint8_t* d_bits, int64_t nb, void* d_ws, int64_t ws_bytes,
-               int64_t region_off, double* d_out, cudaStream_t st);
+               int64_t region_off, double* d_out, cudaStream_t st, int* fault = nullptr);
 
 }  // namespace rt
 }  // namespace tb

@@ -29,6 +29,7 @@
 
 #include <cuda_bf16.h>
 
+#include <atomic>
 #include <mutex>
 
 #include "tc_pass.cuh"
@@ -267,7 +268,7 @@ __global__ void __launch_bounds__(TC_THREADS, TC_CTAS_PER_SM) tc_pass_kernel(con
     float scale = 1.0f;
     int xpre = 0, xpost = 0;
     uint32_t phase = 0;
-    bool waited_out = false;
+    bool mma_pending = false;  // thread 0: MMAs committed whose completion it has not seen
 
     for (; gt < p.ntiles; gt += gridDim.x) {
         const int64_t b = gt >> p.tile_shift;
@@ -350,19 +351,25 @@ __global__ void __launch_bounds__(TC_THREADS, TC_CTAS_PER_SM) tc_pass_kernel(con
                               (prod > 0 || ks > 0) ? 1u : 0u);
             }
             mma_commit(mb);
+            mma_pending = true;
         }
 
         // ---- next tile's loads overlap the MMAs
         const int64_t nx = gt + gridDim.x;
         if (nx < p.ntiles) load_vec(v, vec_addr(nx));
 
-        if (!mbar_wait(mb, phase, tries)) {
+        const bool ok = mbar_wait(mb, phase, tries);
+        if (!ok) {
             atomicAdd(p.fault, 1);
             *s_abort = 1;
-            waited_out = true;
+        } else if (tid == 0) {
+            mma_pending = false;
         }
         phase ^= 1u;
         tc_fence_after();
+        // a warp with a lane whose wait gave up neither reads the accumulator
+        // nor stores: the tile is left as it was (and the call reports the fault)
+        if (__any_sync(0xffffffffu, !ok)) continue;
 
         // ---- output: read D, post-step, maximum, store in place
         float2* dst = p.B + a0;
@@ -412,11 +419,21 @@ __global__ void __launch_bounds__(TC_THREADS, TC_CTAS_PER_SM) tc_pass_kernel(con
         }
     }
     if (cur_b >= 0) flush_max_tc(runmax, p.maxs + cur_b * p.sstride + p.slot + 1);
-    // a thread whose wait gave up waits once more (bounded) for its MMAs
-    if (waited_out) (void)mbar_wait(mb, phase ^ 1u, tries);
+    // Tensor memory may be freed only once no MMA can still write it. Thread 0
+    // issued every MMA; if it has not seen its last commit complete, it waits
+    // once more (bounded). If that wait gives up too, the CTA keeps its tensor
+    // memory (freeing it under a running MMA could corrupt another CTA's
+    // accumulator) and raises TC_TMEM_HELD in the fault word; the host then
+    // refuses further tensor-core passes in this process.
+    if (tid == 0) {
+        bool held = false;
+        if (mma_pending && !mbar_wait(mb, phase ^ 1u, WAIT_TRIES)) held = true;
+        *s_abort = held ? 2 : 0;
+        if (held) atomicOr(p.fault, TC_TMEM_HELD);
+    }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 0 && *s_abort != 2) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
                      "r"((uint32_t)C::TMEM_COLS)
@@ -445,6 +462,17 @@ cudaError_t launch_tc_pass(int precision, const TcParams& p, int grid, cudaStrea
     if (precision == TB_PRECISION_TF32X3) return launch_kind<TB_PRECISION_TF32X3>(p, grid, st);
     return cudaErrorInvalidValue;
 }
+
+namespace {
+std::atomic<bool> g_tc_disabled{false};
+}
+
+int note_faults(int word) {
+    if (word & TC_TMEM_HELD) g_tc_disabled = true;
+    return word & ~TC_TMEM_HELD;
+}
+
+bool tc_passes_disabled() { return g_tc_disabled.load(); }
 
 int* device_fault_word() {
     // looked up once per device (the symbol's address does not change)

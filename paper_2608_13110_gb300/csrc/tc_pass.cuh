@@ -34,4 +34,14 @@ cudaError_t launch_tc_pass(int precision, const TcParams& p, int grid, cudaStrea
 // Device word counting bounded waits that gave up (all kernels of the library).
 int* device_fault_word();
 
+// Bit of a fault word raised by a tensor-core pass CTA that exited without
+// seeing its last MMAs complete and therefore kept its tensor memory.
+constexpr int TC_TMEM_HELD = 1 << 30;
+
+// Record a fault word read back by the host: returns the count of waits that
+// gave up; TC_TMEM_HELD disables tensor-core passes for the rest of the process.
+int note_faults(int word);
+// True once a tensor-core pass has kept its tensor memory (see TC_TMEM_HELD).
+bool tc_passes_disabled();
+
 }  // namespace tb
