@@ -433,8 +433,9 @@ class Server:
     def wait(self, ticket: int, timeout: float = -1.0):
         """(complex128 amplitudes, {latency_s, queue_s, run_s, slot})."""
         st = _ReqStats()
+        st.status = -1  # left as is while the request is still running
         rc = _lib.tb_server_wait(self._h, ticket, float(timeout), ctypes.byref(st))
-        if rc == TB_ETIMEOUT:
+        if rc == TB_ETIMEOUT and st.status == -1:
             raise TimeoutError(f"request {ticket} still running")
         plan, out = self._pending.pop(ticket)
         _check(rc, "tb_server_wait")

@@ -100,7 +100,10 @@ def test_clifford_twin_70_56(tb, oracle_mod, prec):
     nz = p_ref[p_ref > 0]
     assert nz.size > 0
     r = -np.log2(nz[0])
-    np.testing.assert_allclose(np.abs(got) ** 2 * 2.0 ** r, p_ref * 2.0 ** r, atol=1e-3, rtol=0)
+    # |a|^2 carries twice the amplitude's relative error: with the form's
+    # relative-L2 bound B, |a|^2 2^r lies within 2B of 0 or 1; 4B leaves room
+    # for the spread across bitstrings (TF32X3: 8e-5, BF16X3: 6e-4)
+    np.testing.assert_allclose(np.abs(got) ** 2 * 2.0 ** r, p_ref * 2.0 ** r, atol=4 * BOUND[prec], rtol=0)
 
 
 @pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])

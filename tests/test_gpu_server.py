@@ -93,3 +93,41 @@ def test_wait_times_out_and_the_ticket_stays_valid(tb):
         np.testing.assert_allclose(got, ref, rtol=0, atol=1e-5 * np.abs(ref).max())
     finally:
         srv.close()
+
+
+def test_wide_requests_queue_in_arrival_order(tb):
+    """Admission at realistic sizes: two width-28 requests (2 GiB boundary
+    each) and small ones under a 3 GiB budget. The second wide request cannot
+    start until the first has finished; the small requests submitted after it
+    wait behind it (arrival order: the head of the queue is admitted first),
+    while the small request submitted before it runs beside the first wide
+    one. Every result equals the request evaluated alone, and the device
+    memory in use never exceeds the budget."""
+    budget = 3 << 30
+    wide1 = W.random_circuit(30, 56, None, 2, 910)
+    wide2 = W.random_circuit(32, 56, None, 1, 911)
+    small = [W.random_circuit(20, 30, None, 32, 912 + i) for i in range(4)]
+    order = [wide1, small[0], wide2, small[1], small[2], small[3]]
+    plans = [tb.Plan.from_circuit(c) for c in order]
+    assert plans[0].info["boundary_bytes"] == 2 << 30 and plans[2].info["boundary_bytes"] == 2 << 30
+    alone = [p.amplitudes(c.bits) for p, c in zip(plans, order)]
+    srv = tb.Server(hbm_budget_bytes=budget, slots=4)
+    try:
+        tickets = [srv.submit(p, c.bits) for p, c in zip(plans, order)]
+        res = [srv.wait(t, timeout=300.0) for t in tickets]
+        for (got, _), ref in zip(res, alone):
+            assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= TOL
+        st = [s for _, s in res]
+        w1, s0, w2 = st[0], st[1], st[2]
+        # the second wide request waited for the first one's memory
+        assert w2["queue_s"] >= 0.5 * w1["latency_s"]
+        # arrival order: nothing submitted after it was admitted before it
+        for s in st[3:]:
+            assert s["queue_s"] >= w2["queue_s"] - 0.05
+        # the small request submitted before it ran beside the first wide one
+        assert s0["queue_s"] < 0.5 * w1["latency_s"] and s0["latency_s"] < w1["latency_s"]
+        stats = srv.stats()
+        assert stats["peak_bytes_in_use"] <= budget
+        assert stats["completed"] == len(order)
+    finally:
+        srv.close()
