@@ -93,8 +93,8 @@ CallLayout call_layout(const Plan& P) {
     c.red_blocks = (int)std::min<int64_t>(nchunks, MAX_RED_BLOCKS);
     c.partial_bytes = P.open_k ? 0 : align_up((int64_t)c.red_blocks * 16, 256);
     c.boundary_bytes = (int64_t)8 << P.h;
-    c.half_bytes = P.open_k ? ((int64_t)8 << (P.h - 1)) : 0;
-    c.per_b = c.scale_bytes + c.partial_bytes + c.boundary_bytes + c.half_bytes;
+    c.second_bytes = P.open_k ? ((int64_t)8 << P.h) : 0;
+    c.per_b = c.scale_bytes + c.partial_bytes + c.boundary_bytes + c.second_bytes;
     return c;
 }
 
@@ -338,29 +338,41 @@ int run_device(const Plan& P, const uint8_t* d_bits, int64_t nb, void* d_ws, int
 
         if (P.open_k) {  // Algorithm 2: join, late crossings, FP64 output
             const int k = P.open_k;
-            float2* halves = boundary + (int64_t)batch * b_stride;
-            const int64_t h_stride = b_stride / 2;
-            JoinParams jp;
-            jp.B = boundary;
-            jp.b_stride = b_stride;
-            jp.tiles_per_b = b_stride / JOIN_TILE;
-            jp.ntiles = (int64_t)nbat * jp.tiles_per_b;
-            jp.E = tab<float2>(d_ws, L.open_E);
-            {
+            float2* second = boundary + (int64_t)batch * b_stride;  // one 2^h buffer per element
+            float2* cur = boundary;
+            if (k >= JOIN_TC_MIN_K) {  // tensor cores, out of place into the second buffer
+                JoinTcParams jp;
+                jp.in = reinterpret_cast<const float*>(boundary);
+                jp.in_stride = b_stride;
+                jp.out = reinterpret_cast<float*>(second);
+                jp.out_stride = b_stride;
+                jp.Es = tab<uint8_t>(d_ws, L.open_Es);
+                jp.KR = 2 << k;
+                jp.rows = b_stride >> k;
+                jp.nbatch = nbat;
+                jp.fault = fault;
+                const int64_t items = (int64_t)nbat * (jp.rows / 128) * (jp.KR / join_nt(k));
+                ProfScope ps(PC_JOIN, 16.0 * (double)nbat * (double)b_stride, st);
+                TB_CUDA(launch_join_tc(k, jp, (int)std::min<int64_t>(items, nsm), st));
+                cur = second;
+            } else {  // FP32, in place
+                JoinParams jp;
+                jp.B = boundary;
+                jp.b_stride = b_stride;
+                jp.tiles_per_b = b_stride / JOIN_TILE;
+                jp.ntiles = (int64_t)nbat * jp.tiles_per_b;
+                jp.E = tab<float2>(d_ws, L.open_E);
                 ProfScope ps(PC_JOIN, 16.0 * (double)nbat * (double)b_stride, st);
                 TB_CUDA(launch_join(k, jp, (int)std::min<int64_t>(jp.ntiles, 2LL * nsm), st));
             }
             const OpenOp* ops = tab<OpenOp>(d_ws, L.open_ops);
-            float2* cur = boundary;
-            int64_t cur_stride = b_stride;
             for (int i = 0; i + 1 < (int)P.open_seg.size(); ++i) {
-                float2* nxt = (i % 2 == 0) ? halves : boundary;
-                const int64_t nxt_stride = (i % 2 == 0) ? h_stride : b_stride;
+                float2* nxt = cur == boundary ? second : boundary;
                 LateParams lp;
                 lp.in = cur;
-                lp.in_stride = cur_stride;
+                lp.in_stride = b_stride;
                 lp.out = nxt;
-                lp.out_stride = nxt_stride;
+                lp.out_stride = b_stride;
                 lp.out_entries = (int64_t)1 << (P.h - 1 - i);
                 lp.nbatch = nbat;
                 lp.k = k;
@@ -371,11 +383,10 @@ int run_device(const Plan& P, const uint8_t* d_bits, int64_t nb, void* d_ws, int
                 ProfScope ps(PC_LATE, 24.0 * (double)nbat * (double)lp.out_entries, st);
                 TB_CUDA(launch_late(lp, (int)std::min<int64_t>(chunks, 8LL * nsm), st));
                 cur = nxt;
-                cur_stride = nxt_stride;
             }
             OpenFinalParams op;
             op.Z = cur;
-            op.b_stride = cur_stride;
+            op.b_stride = b_stride;
             op.exps = exps;
             op.sstride = sstride;
             op.nslots = c.nslots;

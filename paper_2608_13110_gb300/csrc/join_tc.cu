@@ -1,0 +1,299 @@
+// Join of Algorithm 2 on the tensor cores (sm_103a, tcgen05, 3xTF32).
+//
+// After the sweep of the fixed region the boundary is a matrix B[r][s]: row r
+// = the late crossing bits, column s = the k crossing bits of the early region
+// (address bits 0..k-1, so a row is 2^k consecutive entries). The early
+// region, contracted on the host, is the dense 2^k x 2^k complex matrix E
+// (Sec. 4.3, Algorithm 2), and the join is the complex matrix product
+//     Z[r][y] = sum_s B[r][s] E[s][y].
+// As a real GEMM over the boundary's (re, im) floats, D[r][n] = sum_kk
+// A[r][kk] Bm[kk][n] with kk = 2s + part, n = 2y + part and K = N = 2^(k+1);
+// the host stores Bm = Bm_hi + Bm_lo (TF32) in blocks of JOIN_KC K rows by NT
+// N columns (canonical K-major layout). Here A = A_hi + A_lo is split per
+// element and D = A_lo.Bm_hi + A_hi.Bm_lo + A_hi.Bm_hi accumulates in FP32 in
+// tensor memory (the lo.lo term is dropped), correction products first.
+// The tensor cores' FP32 accumulation drifts over long K (measured: the
+// join's error grew in proportion to K, 1.6e-5 at K = 2048), so each segment
+// of JOIN_SEG_CHUNKS K chunks accumulates in its own tensor-memory sum (two,
+// alternating) and the segments are added in FP32 registers, round to nearest.
+//
+// One CTA per SM (128 threads, persistent). A work item is 128 rows x NT
+// output columns: thread i owns row i (tensor-memory lane i). Per K chunk of
+// JOIN_KC reals: thread 0 copies the Bm block (hi, lo) of the chunk two ahead
+// into one of four shared stages with one bulk copy; every thread splits its
+// row's JOIN_KC floats (loaded one chunk ahead) and writes A_hi / A_lo into
+// one of four tensor-memory stages;
+// thread 0 issues 3 x 4 MMAs (M = 128, N = NT, K = 8) into the segment's sum
+// and commits them to the stage's mbarrier, so the next chunk's loads run
+// while they execute. When a segment's first chunk has been issued, every
+// thread adds the previous segment's sum (its row) into its registers. The
+// epilogue writes the row sums to Z out of place (the input rows are needed
+// by the item's other N tiles).
+//
+// Every wait is bounded; a give-up is counted in the fault word, the CTA
+// stops together (__syncthreads_or), waits (bounded) for its last bulk copy
+// and its last MMAs, and frees tensor memory only when no MMA can still write
+// it (otherwise it raises TC_TMEM_HELD; see tc_pass.cuh).
+
+#include "open_kernels.cuh"
+#include "tc_pass.cuh"
+#include "tc_ptx.cuh"
+
+namespace tb {
+
+namespace {
+
+using namespace tcx;
+
+constexpr int JT_THREADS = 128;
+constexpr uint32_t JT_WAIT_TRIES = 1u << 22;
+constexpr uint32_t JT_TMEM_COLS = 512;
+constexpr int JT_STAGES = 4;         // B blocks in shared memory, A splits in tensor memory
+constexpr uint32_t JT_A_COL = 256;  // A stage s: hi at 256 + 64 s, lo at 256 + 64 s + 32
+// segment sums: columns [0, NT) and [NT, 2 NT), NT <= 128
+constexpr int JT_MIN_SMEM = 120 * 1024;  // more than half the SM: one CTA per SM (it holds 512 columns)
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(bar),
+                 "r"(bytes)
+                 : "memory");
+}
+
+template <int NT>
+__global__ void __launch_bounds__(JT_THREADS, 1) join_tc_kernel(const JoinTcParams p) {
+    constexpr uint32_t PART = (uint32_t)NT * JOIN_KC * 4;  // one of hi / lo
+    constexpr uint32_t BLK = 2 * PART;
+    constexpr uint32_t LBO = 128, SBO = (JOIN_KC / 4) * 128;
+    // D = F32, A and B TF32, both K-major, N >> 3 at bit 17, M >> 4 at bit 24 (M = 128)
+    constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NT >> 3) << 17) |
+                               ((uint32_t)(128 >> 4) << 24);
+    static_assert(2 * NT <= (int)JT_A_COL && JT_A_COL + 64 * JT_STAGES <= JT_TMEM_COLS, "tensor memory plan");
+    extern __shared__ __align__(16) uint8_t dsm[];
+    uint8_t* base = dsm + ((1024u - (smem_u32(dsm) & 1023u)) & 1023u);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + JT_STAGES * BLK);  // b_full[S], mma_done[S]
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * JT_STAGES);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t sB0 = smem_u32(base);
+    const uint32_t bfull0 = smem_u32(bars), mdone0 = bfull0 + 8 * JT_STAGES;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                     "r"(JT_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < JT_STAGES; ++s) {
+            mbar_init(bfull0 + 8 * s, 1);
+            mbar_init(mdone0 + 8 * s, 1);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t lane = tmem + ((uint32_t)(warp * 32) << 16);
+
+    const int KR = p.KR;
+    const int nkc = KR / JOIN_KC, ntn = KR / NT;
+    const int64_t nrb = p.rows / 128;        // row blocks per batch element
+    const int64_t items = (int64_t)p.nbatch * nrb * ntn;
+    // chunk c of this CTA (counted over all its items) uses stage c % JT_STAGES
+    // for its B block (shared memory) and its A split (tensor memory)
+    uint32_t c0 = 0;
+    // thread 0 only: loads issued but not yet seen complete, and the last commit
+    bool load_pending[JT_STAGES];
+    uint32_t load_par[JT_STAGES];
+    for (int s = 0; s < JT_STAGES; ++s) { load_pending[s] = false; load_par[s] = 0; }
+    int64_t last_commit = -1;
+    bool commit_seen = true;
+    bool stop = false;
+
+    auto stage_of = [](uint32_t c) { return c % JT_STAGES; };
+    auto par_of = [](uint32_t c) { return (c / JT_STAGES) & 1u; };
+    // thread 0: copy the B block of chunk kc (global chunk c) into its stage,
+    // once the MMAs that last read that stage (chunk c - JT_STAGES) are done
+    auto issue_b = [&](int nt, int kc, uint32_t c) -> bool {
+        const uint32_t s = stage_of(c);
+        if (c >= JT_STAGES && !mbar_wait(mdone0 + 8 * s, par_of(c - JT_STAGES), JT_WAIT_TRIES)) return false;
+        expect_tx(bfull0 + 8 * s, BLK);
+        bulk_load(sB0 + s * BLK, p.Es + ((int64_t)nt * nkc + kc) * BLK, BLK, bfull0 + 8 * s);
+        load_pending[s] = true;
+        load_par[s] = par_of(c);
+        return true;
+    };
+
+    for (int64_t it = blockIdx.x; it < items && !stop; it += gridDim.x) {
+        const int nt = (int)(it % ntn);
+        const int64_t rbg = it / ntn;
+        const int64_t b = rbg / nrb, rb = rbg - b * nrb;
+        const int64_t row = rb * 128 + tid;
+        const float4* arow = reinterpret_cast<const float4*>(p.in + 2 * (b * p.in_stride + row * (KR / 2)));
+        float acc[NT];
+#pragma unroll
+        for (int c = 0; c < NT; ++c) acc[c] = 0.0f;
+        // add segment sum sg (its last chunk is global chunk cl) to acc
+        auto add_segment = [&](int sg, uint32_t cl) -> bool {
+            const bool ok = mbar_wait(mdone0 + 8 * stage_of(cl), par_of(cl), JT_WAIT_TRIES);
+            if (__syncthreads_or(ok ? 0 : 1)) return false;
+            tc_fence_after();
+#pragma unroll
+            for (int c = 0; c < NT / 16; ++c) {
+                uint32_t r[16];
+                tmem_ld16(lane + NT * (sg & 1) + 16 * c, r);
+                tmem_wait_ld();
+#pragma unroll
+                for (int e = 0; e < 16; ++e) acc[16 * c + e] += __uint_as_float(r[e]);
+            }
+            tc_fence_before();
+            return true;
+        };
+        bool bad = false;
+        if (tid == 0) {
+            bad = !issue_b(nt, 0, c0);
+            if (!bad && nkc > 1) bad = !issue_b(nt, 1, c0 + 1);
+        }
+        float4 an[JOIN_KC / 4];  // the next chunk's floats of this thread's row
+#pragma unroll
+        for (int q = 0; q < JOIN_KC / 4; ++q) an[q] = __ldg(arow + q);
+        for (int kc = 0; kc < nkc; ++kc) {
+            const uint32_t c = c0 + kc, s = stage_of(c);
+            const int sg = kc / JOIN_SEG_CHUNKS;
+            float4 ac[JOIN_KC / 4];
+#pragma unroll
+            for (int q = 0; q < JOIN_KC / 4; ++q) ac[q] = an[q];
+            if (kc + 1 < nkc) {
+#pragma unroll
+                for (int q = 0; q < JOIN_KC / 4; ++q) an[q] = __ldg(arow + (kc + 1) * (JOIN_KC / 4) + q);
+            }
+            if (tid == 0 && !bad && kc + 2 < nkc) bad = !issue_b(nt, kc + 2, c + 2);
+            // the tensor-memory stage was last read by chunk c - JT_STAGES
+            if (c >= JT_STAGES && !bad) bad = !mbar_wait(mdone0 + 8 * s, par_of(c - JT_STAGES), JT_WAIT_TRIES);
+            // split into TF32 hi / lo and store into the stage
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                uint32_t hi[16], lo[16];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 v = ac[4 * half + q];
+                    const float x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const uint32_t h = to_tf32(x[e]);
+                        hi[4 * q + e] = h;
+                        lo[4 * q + e] = to_tf32(x[e] - __uint_as_float(h));
+                    }
+                }
+                tmem_st16(lane + JT_A_COL + 64 * s + 16 * half, hi);
+                tmem_st16(lane + JT_A_COL + 64 * s + 32 + 16 * half, lo);
+            }
+            tmem_wait_st();
+            tc_fence_before();
+            if (__syncthreads_or(bad ? 1 : 0)) {  // a wait gave up
+                if (tid == 0) atomicAdd(p.fault, 1);
+                stop = true;
+                break;
+            }
+            if (tid == 0) {
+                tc_fence_after();
+                if (!mbar_wait(bfull0 + 8 * s, par_of(c), JT_WAIT_TRIES)) {
+                    atomicAdd(p.fault, 1);
+                    stop = true;  // thread 0 alone: the others learn it at the next barrier
+                } else {
+                    load_pending[s] = false;
+                    const uint32_t d = tmem + (uint32_t)(NT * (sg & 1));
+                    const uint32_t bh = sB0 + s * BLK, bl = bh + PART;
+                    const uint32_t a_hi = tmem + JT_A_COL + 64 * s, a_lo = a_hi + 32;
+                    const bool first = kc % JOIN_SEG_CHUNKS == 0;
+#pragma unroll
+                    for (int prod = 0; prod < 3; ++prod) {
+                        const uint32_t a = prod == 0 ? a_lo : a_hi;
+                        const uint32_t bb = prod == 1 ? bl : bh;
+#pragma unroll
+                        for (int ks = 0; ks < JOIN_KC / 8; ++ks)
+                            mma_tf32(d, a + 8 * ks, smem_desc(bb + 256 * ks, LBO, SBO), IDESC,
+                                     (!first || prod > 0 || ks > 0) ? 1u : 0u);
+                    }
+                    mma_commit(mdone0 + 8 * s);
+                    last_commit = c;
+                    commit_seen = false;
+                }
+            }
+            if (__syncthreads_or(stop ? 1 : 0)) {
+                stop = true;
+                break;
+            }
+            // the previous segment's sum is complete once its last chunk's MMAs are
+            if (kc % JOIN_SEG_CHUNKS == 0 && kc > 0 && !add_segment(sg - 1, c - 1)) {
+                if (tid == 0) atomicAdd(p.fault, 1);
+                stop = true;
+                break;
+            }
+        }
+        if (stop) break;
+        c0 += nkc;
+        // epilogue: the last segment, then the row sums
+        if (!add_segment((nkc - 1) / JOIN_SEG_CHUNKS, c0 - 1)) {
+            if (tid == 0) atomicAdd(p.fault, 1);
+            stop = true;
+            break;
+        }
+        if (tid == 0) commit_seen = true;
+        float4* zrow = reinterpret_cast<float4*>(p.out + 2 * (b * p.out_stride + row * (KR / 2)) + nt * NT);
+#pragma unroll
+        for (int c = 0; c < NT / 4; ++c) zrow[c] = make_float4(acc[4 * c], acc[4 * c + 1], acc[4 * c + 2], acc[4 * c + 3]);
+        __syncthreads();  // every thread has read the sums before the next item's MMAs overwrite them
+    }
+
+    // exit: no bulk copy may still write shared memory, and tensor memory is
+    // freed only when no MMA can still write it
+    __shared__ int s_held;
+    if (tid == 0) {
+        for (int s = 0; s < JT_STAGES; ++s)
+            if (load_pending[s]) (void)mbar_wait(bfull0 + 8 * s, load_par[s], JT_WAIT_TRIES);
+        bool held = false;
+        if (!commit_seen && last_commit >= 0 &&
+            !mbar_wait(mdone0 + 8 * stage_of((uint32_t)last_commit), par_of((uint32_t)last_commit), JT_WAIT_TRIES))
+            held = true;
+        if (held) atomicOr(p.fault, TC_TMEM_HELD);
+        s_held = held ? 1 : 0;
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0 && !s_held) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(JT_TMEM_COLS)
+                     : "memory");
+    }
+}
+
+template <int NT>
+cudaError_t launch_nt(const JoinTcParams& p, int grid, cudaStream_t st) {
+    constexpr int need = 1024 + JT_STAGES * (2 * NT * JOIN_KC * 4) + 16 * JT_STAGES + 16;
+    constexpr int smem = need > JT_MIN_SMEM ? need : JT_MIN_SMEM;
+    static_assert(smem <= 227 * 1024, "join smem");
+    const cudaError_t e = cudaFuncSetAttribute(join_tc_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    join_tc_kernel<NT><<<grid, JT_THREADS, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_join_tc(int k, const JoinTcParams& p, int grid, cudaStream_t st) {
+    switch (join_nt(k)) {
+        case 32: return launch_nt<32>(p, grid, st);
+        case 64: return launch_nt<64>(p, grid, st);
+        case 128: return launch_nt<128>(p, grid, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace tb

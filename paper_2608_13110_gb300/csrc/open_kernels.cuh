@@ -41,7 +41,22 @@ struct OpenFinalParams {
     double* out;           // (re, im) of 2^k amplitudes per batch element
 };
 
+// Join on the tensor cores (k >= JOIN_TC_MIN_K), out of place: Z = B.E for
+// every row of every batch element (join_tc.cu).
+struct JoinTcParams {
+    const float* in;       // boundary of batch element 0 as (re, im) floats
+    int64_t in_stride;     // complex entries between batch elements
+    float* out;            // Z of batch element 0
+    int64_t out_stride;
+    const uint8_t* Es;     // split real embedding of E (JOIN_KC x join_nt(k) blocks)
+    int KR;                // 2^(k+1): reals per row
+    int64_t rows;          // rows per batch element, 2^(h-k) (a multiple of 128)
+    int nbatch;
+    int* fault;            // bounded waits that gave up
+};
+
 cudaError_t launch_join(int k, const JoinParams& p, int grid, cudaStream_t st);
+cudaError_t launch_join_tc(int k, const JoinTcParams& p, int grid, cudaStream_t st);
 cudaError_t launch_late(const LateParams& p, int grid, cudaStream_t st);
 cudaError_t launch_open_finalize(const OpenFinalParams& p, int nbatch, cudaStream_t st);
 

@@ -26,6 +26,7 @@
 #include <cmath>
 #include <complex>
 #include <string>
+#include <cstring>
 #include <vector>
 
 #include "tb_plan.h"
@@ -86,6 +87,7 @@ int open_tables(Plan& P, std::string& err) {
     }
     const size_t B = (size_t)1 << k;
     P.open_E.assign(B * B, make_float2(0, 0));
+    std::vector<cd> E64(B * B);
     std::vector<int> js;
     for (size_t s = 0; s < B; ++s) {
         Band band{P, k, q0, std::vector<cd>(B, cd(0.0))};
@@ -102,8 +104,35 @@ int open_tables(Plan& P, std::string& err) {
             band_cz(t, js);
             for (int j : js) band.cz(j, P.w(t, q0 + j));
         }
-        for (size_t y = 0; y < B; ++y)
+        for (size_t y = 0; y < B; ++y) {
             P.open_E[s * B + y] = make_float2((float)band.psi[y].real(), (float)band.psi[y].imag());
+            E64[s * B + y] = band.psi[y];
+        }
+    }
+    // The tensor-core join applies Z[r][y] = sum_s B[r][s] E[s][y] as the real
+    // GEMM D[r][n] = sum_kk A[r][kk] Bm[kk][n], kk = 2s + pi, n = 2y + po
+    // (A = the boundary's (re, im) floats): Bm[2s][2y] = Re E, Bm[2s+1][2y] =
+    // -Im E, Bm[2s][2y+1] = Im E, Bm[2s+1][2y+1] = Re E. Bm = hi + lo (TF32,
+    // from the FP64 E), stored per (N tile, K chunk) block: hi then lo, each
+    // NT x JOIN_KC in the canonical K-major layout.
+    P.open_Es.clear();
+    if (k >= JOIN_TC_MIN_K) {
+        const int KR = 2 << k, NT = join_nt(k), nkc = KR / JOIN_KC;
+        const int64_t part = (int64_t)NT * JOIN_KC * 4;
+        P.open_Es.assign((size_t)(KR / NT) * nkc * 2 * part, 0);
+        for (int n = 0; n < KR; ++n)
+            for (int kk = 0; kk < KR; ++kk) {
+                const cd z = E64[(size_t)(kk >> 1) * B + (n >> 1)];
+                const int po = n & 1, pi = kk & 1;
+                const double val = po == 0 ? (pi == 0 ? z.real() : -z.imag()) : (pi == 0 ? z.imag() : z.real());
+                const int nt = n / NT, kc = kk / JOIN_KC;
+                uint8_t* blk = P.open_Es.data() + ((int64_t)nt * nkc + kc) * 2 * part;
+                const int64_t off = canon_offset(n % NT, kk % JOIN_KC, JOIN_KC, 4);
+                const float vh = round_tf32(val);
+                const float vl = round_tf32(val - (double)vh);
+                std::memcpy(blk + off, &vh, 4);
+                std::memcpy(blk + part + off, &vl, 4);
+            }
     }
     // segments after each late crossing
     P.open_ops.clear();

@@ -569,6 +569,7 @@ int plan_build(Plan& P, int n, int d, const uint8_t* cliff, const uint8_t* tmask
     L.red_top = put((int64_t)P.red_top.size() * 8);
     L.tc_mats = put((int64_t)P.tc_mats.size());
     L.open_E = put((int64_t)P.open_E.size() * 8);
+    L.open_Es = put((int64_t)P.open_Es.size());
     L.open_ops = put((int64_t)P.open_ops.size() * (int64_t)sizeof(OpenOp));
     L.open_seg = put((int64_t)P.open_seg.size() * 4);
     L.total = off;
@@ -589,6 +590,7 @@ int plan_build(Plan& P, int n, int d, const uint8_t* cliff, const uint8_t* tmask
     cp(L.red_top, P.red_top.data(), P.red_top.size() * 8);
     cp(L.tc_mats, P.tc_mats.data(), P.tc_mats.size());
     cp(L.open_E, P.open_E.data(), P.open_E.size() * 8);
+    cp(L.open_Es, P.open_Es.data(), P.open_Es.size());
     cp(L.open_ops, P.open_ops.data(), P.open_ops.size() * sizeof(OpenOp));
     cp(L.open_seg, P.open_seg.data(), P.open_seg.size() * 4);
     return TB_OK;

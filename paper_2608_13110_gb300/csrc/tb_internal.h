@@ -126,6 +126,15 @@ struct OpenOp {
 constexpr int OPEN_MAX_K = 10;          // 2^k x 2^k early-region matrix built on the host
 constexpr int OPEN_CHUNK_BITS = 10;     // late-region kernels work on 1024-entry chunks
 constexpr int JOIN_TILE = 8192;         // join kernel: boundary entries per CTA tile
+// Join on the tensor cores (3xTF32) for k >= JOIN_TC_MIN_K: Z = B.E as a real
+// GEMM with K = N = 2^(k+1); the split E is stored in blocks of JOIN_KC K rows
+// by join_nt(k) N columns, each block in the canonical K-major layout (hi, lo).
+constexpr int JOIN_TC_MIN_K = 4;
+constexpr int JOIN_KC = 32;
+__host__ __device__ constexpr int join_nt(int k) { return (2 << k) < 128 ? (2 << k) : 128; }
+// K chunks accumulated in one tensor-memory sum before it is added in FP32
+// registers (the tensor cores' FP32 accumulation loses precision over long K).
+constexpr int JOIN_SEG_CHUNKS = 4;
 
 // Byte offsets of the device tables inside the workspace head.
 struct TableLayout {
@@ -142,6 +151,7 @@ struct TableLayout {
     int64_t red_top;   // float2[2][2^top][2]  last row: [x] row vectors
     int64_t tc_mats;   // split dense-block matrices of the tensor-core passes
     int64_t open_E;    // float2[2^k][2^k]: early region joined with the first late ops
+    int64_t open_Es;   // split real embedding of open_E for the tensor-core join (k >= JOIN_TC_MIN_K)
     int64_t open_ops;  // OpenOp[]: late-region band operations
     int64_t open_seg;  // int32[h-k+1]: ops of late crossing i are [seg[i], seg[i+1])
     int64_t total;

@@ -43,6 +43,7 @@ struct Plan {
     // open output bits (Algorithm 2): the sweep stops after row n-k-1
     int open_k = 0;
     std::vector<float2> open_E;
+    std::vector<uint8_t> open_Es;  // tensor-core join operand (see JOIN_KC)
     std::vector<OpenOp> open_ops;
     std::vector<int32_t> open_seg;
     std::vector<float2> open_w;  // entangler factor w of each late crossing (-1 for CZ)
@@ -72,6 +73,11 @@ int tc_schedule(Plan& P, std::string& err);
 int plan_build(Plan& P, int n, int d, const uint8_t* cliff, const uint8_t* tmask,
                const tb_gate1q* extra, int n_extra, const double* cphase, const tb_opts* opts,
                std::string& err);
+
+// TF32 rounding (nearest, ties to even) and the canonical K-major operand
+// offset of the tensor-core kernels (tc_plan.cpp).
+float round_tf32(double v);
+int64_t canon_offset(int nn, int kk, int K, int eb);
 
 }  // namespace tb
 

@@ -29,7 +29,7 @@ struct CallLayout {
     int red_blocks = 0;          // reduction blocks
     int64_t partial_bytes = 0;   // reduction partial sums
     int64_t boundary_bytes = 0;  // the boundary, 8 * 2^h
-    int64_t half_bytes = 0;      // open plans: second late-region buffer, 8 * 2^(h-1)
+    int64_t second_bytes = 0;    // open plans: second buffer (join output, late ping-pong), 8 * 2^h
     int64_t per_b = 0;
 };
 

@@ -37,25 +37,6 @@ namespace tb {
 
 using cd = std::complex<double>;
 
-namespace {
-
-struct Chunk {
-    int lo = 0;
-    std::vector<int> steps;  // plan step indices in execution order
-};
-
-// Round to the nearest bfloat16 (ties to even), returned as a float value.
-float round_bf16(double v) {
-    const float f = (float)v;
-    uint32_t u;
-    std::memcpy(&u, &f, 4);
-    if ((u & 0x7f800000u) == 0x7f800000u) return f;  // inf / nan unchanged
-    u = (u + 0x7fffu + ((u >> 16) & 1u)) & 0xffff0000u;
-    float r;
-    std::memcpy(&r, &u, 4);
-    return r;
-}
-
 // Round to the nearest TF32 value (10 explicit mantissa bits, ties to even).
 float round_tf32(double v) {
     const float f = (float)v;
@@ -76,6 +57,26 @@ float round_tf32(double v) {
 int64_t canon_offset(int nn, int kk, int K, int eb) {
     const int T = 16 / eb;
     return ((int64_t)(nn / 8) * (K / T) + kk / T) * 128 + (nn % 8) * 16 + (kk % T) * eb;
+}
+
+
+namespace {
+
+struct Chunk {
+    int lo = 0;
+    std::vector<int> steps;  // plan step indices in execution order
+};
+
+// Round to the nearest bfloat16 (ties to even), returned as a float value.
+float round_bf16(double v) {
+    const float f = (float)v;
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return f;  // inf / nan unchanged
+    u = (u + 0x7fffu + ((u >> 16) & 1u)) & 0xffff0000u;
+    float r;
+    std::memcpy(&r, &u, 4);
+    return r;
 }
 
 // Compose the steps (plan indices, in order) acting on address bits

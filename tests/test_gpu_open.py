@@ -173,3 +173,26 @@ def test_closed_form_70_64_in_the_benchmark_launch(tb, oracle_mod):
     ref = oracle_mod.closed_form_hdiag(c, full_bits(prefixes, c.n, k)).reshape(2, -1)
     for a in range(2):
         assert rel_l2(got[a], ref[a]) < TOL
+
+
+@pytest.mark.parametrize("k", [9, 10])
+def test_tensor_core_join_at_its_largest(tb, oracle_mod, k):
+    """k = 9 and 10 (the join is a 512^2 / 1024^2 complex matrix product on the
+    tensor cores, 3xTF32): n = 30, d = 40 (width 20), two prefixes, six
+    sampled suffixes each against the FP64 naive boundary, and every suffix
+    against the state vector of an n = 16, d = 40 circuit."""
+    c = W.slice_30_40(nb=0)
+    rng = np.random.default_rng(4400 + k)
+    prefixes = rng.integers(0, 2, size=(2, c.n - k), dtype=np.uint8)
+    got = tb.Plan.from_circuit(c, open_k=k).amplitudes(prefixes)
+    ys = rng.choice(1 << k, size=6, replace=False)
+    for i in range(2):
+        bits = full_bits(prefixes[i:i + 1], c.n, k)[ys]
+        ref = oracle_mod.nb_amplitudes(c.n, c.d, oracle_mod.circuit_gates(c), bits)
+        assert rel_l2(got[i, ys], ref) < TOL
+    c2 = W.random_circuit(16, 40, None, 0, 4500 + k)
+    pre2 = rng.integers(0, 2, size=(2, 16 - k), dtype=np.uint8)
+    got2 = tb.Plan.from_circuit(c2, open_k=k).amplitudes(pre2)
+    ref2 = oracle_mod.sv_amplitudes(16, 40, oracle_mod.circuit_gates(c2), full_bits(pre2, 16, k)).reshape(2, -1)
+    for i in range(2):
+        assert rel_l2(got2[i], ref2[i]) < TOL
