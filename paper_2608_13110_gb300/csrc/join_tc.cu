@@ -45,10 +45,12 @@ namespace {
 
 using namespace tcx;
 
-constexpr int JT_THREADS = 128;
+constexpr int JT_ROWS = 128;      // row warps 0..3: thread i owns row i (tensor-memory lane i)
+constexpr int JT_THREADS = JT_ROWS + 32;  // + the MMA warp
 constexpr uint32_t JT_WAIT_TRIES = 1u << 22;
 constexpr uint32_t JT_TMEM_COLS = 512;
 constexpr int JT_STAGES = 4;         // B blocks in shared memory, A splits in tensor memory
+constexpr int JT_AHEAD = 2;          // B copies issued this many chunks ahead of the MMAs
 constexpr uint32_t JT_A_COL = 256;  // A stage s: hi at 256 + 64 s, lo at 256 + 64 s + 32
 // segment sums: columns [0, NT) and [NT, 2 NT), NT <= 128
 constexpr int JT_MIN_SMEM = 120 * 1024;  // more than half the SM: one CTA per SM (it holds 512 columns)
@@ -77,11 +79,16 @@ __global__ void __launch_bounds__(JT_THREADS, 1) join_tc_kernel(const JoinTcPara
     static_assert(2 * NT <= (int)JT_A_COL && JT_A_COL + 64 * JT_STAGES <= JT_TMEM_COLS, "tensor memory plan");
     extern __shared__ __align__(16) uint8_t dsm[];
     uint8_t* base = dsm + ((1024u - (smem_u32(dsm) & 1023u)) & 1023u);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(base + JT_STAGES * BLK);  // b_full[S], mma_done[S]
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * JT_STAGES);
+    // mbarriers: b_full[S] (bulk copy landed), a_full[S] (128 rows split into
+    // the stage), mma_done[S] (the stage's MMAs finished), d_free[2] (a segment
+    // sum has been read by every row)
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + JT_STAGES * BLK);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 3 * JT_STAGES + 2);
+    int* s_stop = reinterpret_cast<int*>(tslot + 1);
     const int tid = threadIdx.x, warp = tid >> 5;
     const uint32_t sB0 = smem_u32(base);
-    const uint32_t bfull0 = smem_u32(bars), mdone0 = bfull0 + 8 * JT_STAGES;
+    const uint32_t bfull0 = smem_u32(bars), afull0 = bfull0 + 8 * JT_STAGES, mdone0 = afull0 + 8 * JT_STAGES,
+                   dfree0 = mdone0 + 8 * JT_STAGES;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
@@ -92,45 +99,111 @@ __global__ void __launch_bounds__(JT_THREADS, 1) join_tc_kernel(const JoinTcPara
     if (tid == 0) {
         for (int s = 0; s < JT_STAGES; ++s) {
             mbar_init(bfull0 + 8 * s, 1);
+            mbar_init(afull0 + 8 * s, JT_ROWS);
             mbar_init(mdone0 + 8 * s, 1);
         }
+        mbar_init(dfree0, JT_ROWS);
+        mbar_init(dfree0 + 8, JT_ROWS);
+        *s_stop = 0;
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-    const uint32_t lane = tmem + ((uint32_t)(warp * 32) << 16);
 
     const int KR = p.KR;
     const int nkc = KR / JOIN_KC, ntn = KR / NT;
-    const int64_t nrb = p.rows / 128;        // row blocks per batch element
+    const int nseg = (nkc + JOIN_SEG_CHUNKS - 1) / JOIN_SEG_CHUNKS;
+    const int64_t nrb = p.rows / 128;  // row blocks per batch element
     const int64_t items = (int64_t)p.nbatch * nrb * ntn;
-    // chunk c of this CTA (counted over all its items) uses stage c % JT_STAGES
-    // for its B block (shared memory) and its A split (tensor memory)
-    uint32_t c0 = 0;
-    // thread 0 only: loads issued but not yet seen complete, and the last commit
-    bool load_pending[JT_STAGES];
-    uint32_t load_par[JT_STAGES];
-    for (int s = 0; s < JT_STAGES; ++s) { load_pending[s] = false; load_par[s] = 0; }
-    int64_t last_commit = -1;
-    bool commit_seen = true;
-    bool stop = false;
-
+    // Chunk c of this CTA (counted over all its items) uses stage c % S for its
+    // B block (shared memory) and A split (tensor memory); segment g (counted
+    // over all items) accumulates in D[g % 2].
     auto stage_of = [](uint32_t c) { return c % JT_STAGES; };
     auto par_of = [](uint32_t c) { return (c / JT_STAGES) & 1u; };
-    // thread 0: copy the B block of chunk kc (global chunk c) into its stage,
-    // once the MMAs that last read that stage (chunk c - JT_STAGES) are done
-    auto issue_b = [&](int nt, int kc, uint32_t c) -> bool {
-        const uint32_t s = stage_of(c);
-        if (c >= JT_STAGES && !mbar_wait(mdone0 + 8 * s, par_of(c - JT_STAGES), JT_WAIT_TRIES)) return false;
-        expect_tx(bfull0 + 8 * s, BLK);
-        bulk_load(sB0 + s * BLK, p.Es + ((int64_t)nt * nkc + kc) * BLK, BLK, bfull0 + 8 * s);
-        load_pending[s] = true;
-        load_par[s] = par_of(c);
-        return true;
+    auto stopped = [&]() { return *(volatile int*)s_stop != 0; };
+    auto give_up = [&]() {
+        if (atomicExch(s_stop, 1) == 0) atomicAdd(p.fault, 1);
     };
 
-    for (int64_t it = blockIdx.x; it < items && !stop; it += gridDim.x) {
+    __shared__ int s_held;
+    if (warp == JT_ROWS / 32) {
+        // ------------------------------------------------ MMA warp (lane 0)
+        if ((tid & 31) == 0) {
+        uint32_t c = 0, g = 0;
+        int64_t last_commit = -1;
+        bool loaded[JT_STAGES];     // a copy issued into the stage and not yet consumed
+        uint32_t load_par[JT_STAGES];
+        for (int s = 0; s < JT_STAGES; ++s) { loaded[s] = false; load_par[s] = 0; }
+        for (int64_t it = blockIdx.x; it < items && !stopped(); it += gridDim.x) {
+            const int nt = (int)(it % ntn);
+            // B copies run JT_AHEAD chunks ahead of the MMAs (within the item); the
+            // stage a copy reuses was last read by the MMAs of the chunk
+            // JT_STAGES before it, two chunks older than the ones in flight
+            auto issue = [&](int kc) -> bool {
+                const uint32_t cc = c + kc, s = stage_of(cc);
+                if (cc >= JT_STAGES && !mbar_wait(mdone0 + 8 * s, par_of(cc - JT_STAGES), JT_WAIT_TRIES)) return false;
+                expect_tx(bfull0 + 8 * s, BLK);
+                bulk_load(sB0 + s * BLK, p.Es + ((int64_t)nt * nkc + kc) * BLK, BLK, bfull0 + 8 * s);
+                loaded[s] = true;
+                load_par[s] = par_of(cc);
+                return true;
+            };
+            bool ok = true;
+            for (int kc = 0; kc < JT_AHEAD && kc < nkc && ok; ++kc) ok = issue(kc);
+            for (int kc = 0; kc < nkc && ok; ++kc) {
+                const uint32_t cc = c + kc, s = stage_of(cc);
+                if (kc + JT_AHEAD < nkc) ok = issue(kc + JT_AHEAD);
+                const int sg = kc / JOIN_SEG_CHUNKS;
+                const uint32_t gg = g + sg;
+                const bool first = kc % JOIN_SEG_CHUNKS == 0;
+                // a segment's first MMA overwrites D[gg % 2], last read for segment gg - 2
+                if (ok && first && gg >= 2) ok = mbar_wait(dfree0 + 8 * (gg & 1u), ((gg - 2) >> 1) & 1u, JT_WAIT_TRIES);
+                if (ok) ok = mbar_wait(bfull0 + 8 * s, par_of(cc), JT_WAIT_TRIES);
+                if (ok) ok = mbar_wait(afull0 + 8 * s, par_of(cc), JT_WAIT_TRIES);
+                if (!ok) break;
+                loaded[s] = false;
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(NT * (gg & 1u));
+                const uint32_t bh = sB0 + s * BLK, bl = bh + PART;
+                const uint32_t a_hi = tmem + JT_A_COL + 64 * s, a_lo = a_hi + 32;
+#pragma unroll
+                for (int prod = 0; prod < 3; ++prod) {
+                    const uint32_t a = prod == 0 ? a_lo : a_hi;
+                    const uint32_t bb = prod == 1 ? bl : bh;
+#pragma unroll
+                    for (int ks = 0; ks < JOIN_KC / 8; ++ks)
+                        mma_tf32(d, a + 8 * ks, smem_desc(bb + 256 * ks, LBO, SBO), IDESC,
+                                 (!first || prod > 0 || ks > 0) ? 1u : 0u);
+                }
+                mma_commit(mdone0 + 8 * s);
+                last_commit = cc;
+            }
+            if (!ok) {
+                give_up();
+                break;
+            }
+            c += nkc;
+            g += nseg;
+        }
+        // exit: the copies issued must land, and the MMAs must finish before
+        // the tensor memory can be freed
+        for (int s = 0; s < JT_STAGES; ++s)
+            if (loaded[s]) (void)mbar_wait(bfull0 + 8 * s, load_par[s], JT_WAIT_TRIES);
+        bool held = false;
+        if (last_commit >= 0 &&
+            !mbar_wait(mdone0 + 8 * stage_of((uint32_t)last_commit), par_of((uint32_t)last_commit), JT_WAIT_TRIES))
+            held = true;
+        if (held) atomicOr(p.fault, TC_TMEM_HELD);
+        s_held = held ? 1 : 0;
+        }
+        __syncwarp();
+    } else {
+    // ---------------------------------------------------- row warps (0..3)
+    const uint32_t lane = tmem + ((uint32_t)(warp * 32) << 16);
+    uint32_t c = 0, g = 0;
+    bool ok = true;
+    for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x) {
         const int nt = (int)(it % ntn);
         const int64_t rbg = it / ntn;
         const int64_t b = rbg / nrb, rb = rbg - b * nrb;
@@ -138,34 +211,30 @@ __global__ void __launch_bounds__(JT_THREADS, 1) join_tc_kernel(const JoinTcPara
         const float4* arow = reinterpret_cast<const float4*>(p.in + 2 * (b * p.in_stride + row * (KR / 2)));
         float acc[NT];
 #pragma unroll
-        for (int c = 0; c < NT; ++c) acc[c] = 0.0f;
-        // add segment sum sg (its last chunk is global chunk cl) to acc
-        auto add_segment = [&](int sg, uint32_t cl) -> bool {
-            const bool ok = mbar_wait(mdone0 + 8 * stage_of(cl), par_of(cl), JT_WAIT_TRIES);
-            if (__syncthreads_or(ok ? 0 : 1)) return false;
+        for (int e = 0; e < NT; ++e) acc[e] = 0.0f;
+        // add segment gg (its last chunk is cl) to acc, then free its sum
+        // (the decisions below are warp-uniform: tcgen05.ld / st are warp-collective)
+        auto add_segment = [&](uint32_t gg, uint32_t cl) -> bool {
+            const bool w = mbar_wait(mdone0 + 8 * stage_of(cl), par_of(cl), JT_WAIT_TRIES);
+            if (__any_sync(0xffffffffu, !w)) return false;
             tc_fence_after();
 #pragma unroll
-            for (int c = 0; c < NT / 16; ++c) {
+            for (int q = 0; q < NT / 16; ++q) {
                 uint32_t r[16];
-                tmem_ld16(lane + NT * (sg & 1) + 16 * c, r);
+                tmem_ld16(lane + NT * (gg & 1u) + 16 * q, r);
                 tmem_wait_ld();
 #pragma unroll
-                for (int e = 0; e < 16; ++e) acc[16 * c + e] += __uint_as_float(r[e]);
+                for (int e = 0; e < 16; ++e) acc[16 * q + e] += __uint_as_float(r[e]);
             }
             tc_fence_before();
+            mbar_arrive(dfree0 + 8 * (gg & 1u));
             return true;
         };
-        bool bad = false;
-        if (tid == 0) {
-            bad = !issue_b(nt, 0, c0);
-            if (!bad && nkc > 1) bad = !issue_b(nt, 1, c0 + 1);
-        }
-        float4 an[JOIN_KC / 4];  // the next chunk's floats of this thread's row
+        float4 an[JOIN_KC / 4];
 #pragma unroll
         for (int q = 0; q < JOIN_KC / 4; ++q) an[q] = __ldg(arow + q);
         for (int kc = 0; kc < nkc; ++kc) {
-            const uint32_t c = c0 + kc, s = stage_of(c);
-            const int sg = kc / JOIN_SEG_CHUNKS;
+            const uint32_t cc = c + kc, s = stage_of(cc);
             float4 ac[JOIN_KC / 4];
 #pragma unroll
             for (int q = 0; q < JOIN_KC / 4; ++q) ac[q] = an[q];
@@ -173,10 +242,12 @@ __global__ void __launch_bounds__(JT_THREADS, 1) join_tc_kernel(const JoinTcPara
 #pragma unroll
                 for (int q = 0; q < JOIN_KC / 4; ++q) an[q] = __ldg(arow + (kc + 1) * (JOIN_KC / 4) + q);
             }
-            if (tid == 0 && !bad && kc + 2 < nkc) bad = !issue_b(nt, kc + 2, c + 2);
-            // the tensor-memory stage was last read by chunk c - JT_STAGES
-            if (c >= JT_STAGES && !bad) bad = !mbar_wait(mdone0 + 8 * s, par_of(c - JT_STAGES), JT_WAIT_TRIES);
-            // split into TF32 hi / lo and store into the stage
+            // the stage's tensor memory was last read by the MMAs of chunk cc - S
+            const bool w = cc < JT_STAGES || mbar_wait(mdone0 + 8 * s, par_of(cc - JT_STAGES), JT_WAIT_TRIES);
+            if (__any_sync(0xffffffffu, !w || stopped())) {
+                ok = false;
+                break;
+            }
 #pragma unroll
             for (int half = 0; half < 2; ++half) {
                 uint32_t hi[16], lo[16];
@@ -196,75 +267,29 @@ __global__ void __launch_bounds__(JT_THREADS, 1) join_tc_kernel(const JoinTcPara
             }
             tmem_wait_st();
             tc_fence_before();
-            if (__syncthreads_or(bad ? 1 : 0)) {  // a wait gave up
-                if (tid == 0) atomicAdd(p.fault, 1);
-                stop = true;
-                break;
-            }
-            if (tid == 0) {
-                tc_fence_after();
-                if (!mbar_wait(bfull0 + 8 * s, par_of(c), JT_WAIT_TRIES)) {
-                    atomicAdd(p.fault, 1);
-                    stop = true;  // thread 0 alone: the others learn it at the next barrier
-                } else {
-                    load_pending[s] = false;
-                    const uint32_t d = tmem + (uint32_t)(NT * (sg & 1));
-                    const uint32_t bh = sB0 + s * BLK, bl = bh + PART;
-                    const uint32_t a_hi = tmem + JT_A_COL + 64 * s, a_lo = a_hi + 32;
-                    const bool first = kc % JOIN_SEG_CHUNKS == 0;
-#pragma unroll
-                    for (int prod = 0; prod < 3; ++prod) {
-                        const uint32_t a = prod == 0 ? a_lo : a_hi;
-                        const uint32_t bb = prod == 1 ? bl : bh;
-#pragma unroll
-                        for (int ks = 0; ks < JOIN_KC / 8; ++ks)
-                            mma_tf32(d, a + 8 * ks, smem_desc(bb + 256 * ks, LBO, SBO), IDESC,
-                                     (!first || prod > 0 || ks > 0) ? 1u : 0u);
-                    }
-                    mma_commit(mdone0 + 8 * s);
-                    last_commit = c;
-                    commit_seen = false;
-                }
-            }
-            if (__syncthreads_or(stop ? 1 : 0)) {
-                stop = true;
-                break;
-            }
+            mbar_arrive(afull0 + 8 * s);
             // the previous segment's sum is complete once its last chunk's MMAs are
-            if (kc % JOIN_SEG_CHUNKS == 0 && kc > 0 && !add_segment(sg - 1, c - 1)) {
-                if (tid == 0) atomicAdd(p.fault, 1);
-                stop = true;
+            if (kc % JOIN_SEG_CHUNKS == 0 && kc > 0 && !add_segment(g + kc / JOIN_SEG_CHUNKS - 1, cc - 1)) {
+                ok = false;
                 break;
             }
         }
-        if (stop) break;
-        c0 += nkc;
-        // epilogue: the last segment, then the row sums
-        if (!add_segment((nkc - 1) / JOIN_SEG_CHUNKS, c0 - 1)) {
-            if (tid == 0) atomicAdd(p.fault, 1);
-            stop = true;
+        if (!ok) break;
+        c += nkc;
+        g += nseg;
+        if (!add_segment(g - 1, c - 1)) {
+            ok = false;
             break;
         }
-        if (tid == 0) commit_seen = true;
         float4* zrow = reinterpret_cast<float4*>(p.out + 2 * (b * p.out_stride + row * (KR / 2)) + nt * NT);
 #pragma unroll
-        for (int c = 0; c < NT / 4; ++c) zrow[c] = make_float4(acc[4 * c], acc[4 * c + 1], acc[4 * c + 2], acc[4 * c + 3]);
-        __syncthreads();  // every thread has read the sums before the next item's MMAs overwrite them
+        for (int q = 0; q < NT / 4; ++q) zrow[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
     }
+    if (!ok) give_up();
+    }  // row warps
 
-    // exit: no bulk copy may still write shared memory, and tensor memory is
-    // freed only when no MMA can still write it
-    __shared__ int s_held;
-    if (tid == 0) {
-        for (int s = 0; s < JT_STAGES; ++s)
-            if (load_pending[s]) (void)mbar_wait(bfull0 + 8 * s, load_par[s], JT_WAIT_TRIES);
-        bool held = false;
-        if (!commit_seen && last_commit >= 0 &&
-            !mbar_wait(mdone0 + 8 * stage_of((uint32_t)last_commit), par_of((uint32_t)last_commit), JT_WAIT_TRIES))
-            held = true;
-        if (held) atomicOr(p.fault, TC_TMEM_HELD);
-        s_held = held ? 1 : 0;
-    }
+    // exit: the MMA thread has seen its copies land and its MMAs finish (or
+    // raised TC_TMEM_HELD); only then is the tensor memory freed
     tc_fence_before();
     __syncthreads();
     if (warp == 0 && !s_held) {
@@ -276,7 +301,7 @@ __global__ void __launch_bounds__(JT_THREADS, 1) join_tc_kernel(const JoinTcPara
 
 template <int NT>
 cudaError_t launch_nt(const JoinTcParams& p, int grid, cudaStream_t st) {
-    constexpr int need = 1024 + JT_STAGES * (2 * NT * JOIN_KC * 4) + 16 * JT_STAGES + 16;
+    constexpr int need = 1024 + JT_STAGES * (2 * NT * JOIN_KC * 4) + 8 * (3 * JT_STAGES + 2) + 16;
     constexpr int smem = need > JT_MIN_SMEM ? need : JT_MIN_SMEM;
     static_assert(smem <= 227 * 1024, "join smem");
     const cudaError_t e = cudaFuncSetAttribute(join_tc_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

@@ -21,6 +21,10 @@ __device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(a) : "memory");
+}
+
 // Bounded wait for the phase with the given parity; false if it gave up.
 __device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, uint32_t tries) {
     for (uint32_t it = 0; it < tries; ++it) {
