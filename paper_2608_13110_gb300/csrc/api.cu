@@ -352,8 +352,21 @@ int run_device(const Plan& P, const uint8_t* d_bits, int64_t nb, void* d_ws, int
                 jp.nbatch = nbat;
                 jp.fault = fault;
                 const int64_t items = (int64_t)nbat * (jp.rows / 128) * (jp.KR / join_nt(k));
+                CUtensorMap amap;
+                {
+                    EncodeTiledFn enc = encode_tiled_fn();
+                    if (!enc) return fail(TB_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+                    const cuuint64_t dim[2] = {(cuuint64_t)jp.KR, (cuuint64_t)(jp.rows * nbat)};
+                    const cuuint64_t stride[1] = {(cuuint64_t)jp.KR * 4};
+                    const cuuint32_t box[2] = {(cuuint32_t)JOIN_KC, 128}, estr[2] = {1, 1};
+                    const CUresult r = enc(&amap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, boundary, dim, stride, box, estr,
+                                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                    if (r != CUDA_SUCCESS)
+                        return fail(TB_ECUDA, "cuTensorMapEncodeTiled failed for the join (" + std::to_string((int)r) + ")");
+                }
                 ProfScope ps(PC_JOIN, 16.0 * (double)nbat * (double)b_stride, st);
-                TB_CUDA(launch_join_tc(k, jp, (int)std::min<int64_t>(items, nsm), st));
+                TB_CUDA(launch_join_tc(k, jp, amap, (int)std::min<int64_t>(items, nsm), st));
                 cur = second;
             } else {  // FP32, in place
                 JoinParams jp;

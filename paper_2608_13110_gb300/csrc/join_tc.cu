@@ -35,6 +35,8 @@
 // and its last MMAs, and frees tensor memory only when no MMA can still write
 // it (otherwise it raises TC_TMEM_HELD; see tc_pass.cuh).
 
+#include <cuda.h>
+
 #include "open_kernels.cuh"
 #include "tc_pass.cuh"
 #include "tc_ptx.cuh"
@@ -62,6 +64,14 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
         : "memory");
 }
 
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* m, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(m)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
 __device__ __forceinline__ void expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(bar),
                  "r"(bytes)
@@ -69,9 +79,12 @@ __device__ __forceinline__ void expect_tx(uint32_t bar, uint32_t bytes) {
 }
 
 template <int NT>
-__global__ void __launch_bounds__(JT_THREADS, 1) join_tc_kernel(const JoinTcParams p) {
+__global__ void __launch_bounds__(JT_THREADS, 1)
+    join_tc_kernel(const JoinTcParams p, const __grid_constant__ CUtensorMap amap) {
     constexpr uint32_t PART = (uint32_t)NT * JOIN_KC * 4;  // one of hi / lo
     constexpr uint32_t BLK = 2 * PART;
+    constexpr uint32_t ABYTES = 128 * JOIN_KC * 4;          // 128 rows x JOIN_KC floats
+    constexpr uint32_t STG = BLK + ABYTES;                   // one stage: B block, then A rows
     constexpr uint32_t LBO = 128, SBO = (JOIN_KC / 4) * 128;
     // D = F32, A and B TF32, both K-major, N >> 3 at bit 17, M >> 4 at bit 24 (M = 128)
     constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NT >> 3) << 17) |
@@ -82,7 +95,7 @@ __global__ void __launch_bounds__(JT_THREADS, 1) join_tc_kernel(const JoinTcPara
     // mbarriers: b_full[S] (bulk copy landed), a_full[S] (128 rows split into
     // the stage), mma_done[S] (the stage's MMAs finished), d_free[2] (a segment
     // sum has been read by every row)
-    uint64_t* bars = reinterpret_cast<uint64_t*>(base + JT_STAGES * BLK);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + JT_STAGES * STG);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 3 * JT_STAGES + 2);
     int* s_stop = reinterpret_cast<int*>(tslot + 1);
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -140,11 +153,15 @@ __global__ void __launch_bounds__(JT_THREADS, 1) join_tc_kernel(const JoinTcPara
             // B copies run JT_AHEAD chunks ahead of the MMAs (within the item); the
             // stage a copy reuses was last read by the MMAs of the chunk
             // JT_STAGES before it, two chunks older than the ones in flight
+            const int arow0 = (int)((it / ntn) * 128);  // first row of the item (batch elements are contiguous)
             auto issue = [&](int kc) -> bool {
                 const uint32_t cc = c + kc, s = stage_of(cc);
+                // the stage was last used by chunk cc - S: its MMAs (and so the
+                // rows' reads of its A tile) must be done
                 if (cc >= JT_STAGES && !mbar_wait(mdone0 + 8 * s, par_of(cc - JT_STAGES), JT_WAIT_TRIES)) return false;
-                expect_tx(bfull0 + 8 * s, BLK);
-                bulk_load(sB0 + s * BLK, p.Es + ((int64_t)nt * nkc + kc) * BLK, BLK, bfull0 + 8 * s);
+                expect_tx(bfull0 + 8 * s, STG);
+                bulk_load(sB0 + s * STG, p.Es + ((int64_t)nt * nkc + kc) * BLK, BLK, bfull0 + 8 * s);
+                tma_load_2d(sB0 + s * STG + BLK, &amap, kc * JOIN_KC, arow0, bfull0 + 8 * s);
                 loaded[s] = true;
                 load_par[s] = par_of(cc);
                 return true;
@@ -165,7 +182,7 @@ __global__ void __launch_bounds__(JT_THREADS, 1) join_tc_kernel(const JoinTcPara
                 loaded[s] = false;
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(NT * (gg & 1u));
-                const uint32_t bh = sB0 + s * BLK, bl = bh + PART;
+                const uint32_t bh = sB0 + s * STG, bl = bh + PART;
                 const uint32_t a_hi = tmem + JT_A_COL + 64 * s, a_lo = a_hi + 32;
 #pragma unroll
                 for (int prod = 0; prod < 3; ++prod) {
@@ -208,7 +225,6 @@ __global__ void __launch_bounds__(JT_THREADS, 1) join_tc_kernel(const JoinTcPara
         const int64_t rbg = it / ntn;
         const int64_t b = rbg / nrb, rb = rbg - b * nrb;
         const int64_t row = rb * 128 + tid;
-        const float4* arow = reinterpret_cast<const float4*>(p.in + 2 * (b * p.in_stride + row * (KR / 2)));
         float acc[NT];
 #pragma unroll
         for (int e = 0; e < NT; ++e) acc[e] = 0.0f;
@@ -230,24 +246,21 @@ __global__ void __launch_bounds__(JT_THREADS, 1) join_tc_kernel(const JoinTcPara
             mbar_arrive(dfree0 + 8 * (gg & 1u));
             return true;
         };
-        float4 an[JOIN_KC / 4];
-#pragma unroll
-        for (int q = 0; q < JOIN_KC / 4; ++q) an[q] = __ldg(arow + q);
         for (int kc = 0; kc < nkc; ++kc) {
             const uint32_t cc = c + kc, s = stage_of(cc);
-            float4 ac[JOIN_KC / 4];
-#pragma unroll
-            for (int q = 0; q < JOIN_KC / 4; ++q) ac[q] = an[q];
-            if (kc + 1 < nkc) {
-#pragma unroll
-                for (int q = 0; q < JOIN_KC / 4; ++q) an[q] = __ldg(arow + (kc + 1) * (JOIN_KC / 4) + q);
-            }
-            // the stage's tensor memory was last read by the MMAs of chunk cc - S
-            const bool w = cc < JT_STAGES || mbar_wait(mdone0 + 8 * s, par_of(cc - JT_STAGES), JT_WAIT_TRIES);
+            // the stage's A tile (and B block) landed; its tensor memory was
+            // freed by the MMAs of chunk cc - S before the copies were issued
+            const bool w = mbar_wait(bfull0 + 8 * s, par_of(cc), JT_WAIT_TRIES);
             if (__any_sync(0xffffffffu, !w || stopped())) {
                 ok = false;
                 break;
             }
+            // row tid of the A tile: 128 bytes, 16-byte chunks XOR-swizzled by row % 8
+            const uint8_t* arow_s = base + s * STG + BLK + tid * (JOIN_KC * 4);
+            float4 ac[JOIN_KC / 4];
+#pragma unroll
+            for (int q = 0; q < JOIN_KC / 4; ++q)
+                ac[q] = *reinterpret_cast<const float4*>(arow_s + 16 * (q ^ (tid & 7)));
 #pragma unroll
             for (int half = 0; half < 2; ++half) {
                 uint32_t hi[16], lo[16];
@@ -300,23 +313,23 @@ __global__ void __launch_bounds__(JT_THREADS, 1) join_tc_kernel(const JoinTcPara
 }
 
 template <int NT>
-cudaError_t launch_nt(const JoinTcParams& p, int grid, cudaStream_t st) {
-    constexpr int need = 1024 + JT_STAGES * (2 * NT * JOIN_KC * 4) + 8 * (3 * JT_STAGES + 2) + 16;
+cudaError_t launch_nt(const JoinTcParams& p, const CUtensorMap& m, int grid, cudaStream_t st) {
+    constexpr int need = 1024 + JT_STAGES * (2 * NT * JOIN_KC * 4 + 128 * JOIN_KC * 4) + 8 * (3 * JT_STAGES + 2) + 16;
     constexpr int smem = need > JT_MIN_SMEM ? need : JT_MIN_SMEM;
     static_assert(smem <= 227 * 1024, "join smem");
     const cudaError_t e = cudaFuncSetAttribute(join_tc_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    join_tc_kernel<NT><<<grid, JT_THREADS, smem, st>>>(p);
+    join_tc_kernel<NT><<<grid, JT_THREADS, smem, st>>>(p, m);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_join_tc(int k, const JoinTcParams& p, int grid, cudaStream_t st) {
+cudaError_t launch_join_tc(int k, const JoinTcParams& p, const CUtensorMap& amap, int grid, cudaStream_t st) {
     switch (join_nt(k)) {
-        case 32: return launch_nt<32>(p, grid, st);
-        case 64: return launch_nt<64>(p, grid, st);
-        case 128: return launch_nt<128>(p, grid, st);
+        case 32: return launch_nt<32>(p, amap, grid, st);
+        case 64: return launch_nt<64>(p, amap, grid, st);
+        case 128: return launch_nt<128>(p, amap, grid, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "tb_internal.h"
@@ -56,7 +57,9 @@ struct JoinTcParams {
 };
 
 cudaError_t launch_join(int k, const JoinParams& p, int grid, cudaStream_t st);
-cudaError_t launch_join_tc(int k, const JoinTcParams& p, int grid, cudaStream_t st);
+// amap: 2-D tensor map over the rows of every batch element ([rows * nbatch]
+// x [2^(k+1) floats]), box JOIN_KC floats x 128 rows, 128-byte swizzle.
+cudaError_t launch_join_tc(int k, const JoinTcParams& p, const CUtensorMap& amap, int grid, cudaStream_t st);
 cudaError_t launch_late(const LateParams& p, int grid, cudaStream_t st);
 cudaError_t launch_open_finalize(const OpenFinalParams& p, int nbatch, cudaStream_t st);
 
