@@ -259,6 +259,7 @@ int run_device(const Plan& P, const uint8_t* d_bits, int64_t nb, void* d_ws, int
     const int64_t b_stride = (int64_t)1 << P.h;
     const int nsm = num_sms();
     const StepG* steps = tab<StepG>(d_ws, L.steps);
+    const StepG* pass_steps = tab<StepG>(d_ws, L.pass_steps);
     const int xstride = (int)in_row(P);  // bytes between the input rows of two batch elements
 
     for (int64_t b0 = 0; b0 < nb; b0 += batch) {
@@ -318,7 +319,7 @@ int run_device(const Plan& P, const uint8_t* d_bits, int64_t nb, void* d_ws, int
             pp.h = P.h; pp.lo = d.lo; pp.n = xstride;
             pp.tile_shift = P.h - TILE_BITS;
             pp.ntiles = (int64_t)nbat << pp.tile_shift;
-            pp.steps = steps + d.step0;
+            pp.steps = pass_steps + d.pstep0;
             pp.xs_step0 = d.xs_step[0]; pp.xs_q0 = d.xs_q[0];
             pp.xs_step1 = d.xs_step[1]; pp.xs_q1 = d.xs_q[1];
             pp.bits = bits;
@@ -542,6 +543,7 @@ int tb_plan_info(const tb_plan* plan, tb_plan_info_t* info) {
     info->boundary_bytes = (int64_t)8 << P.h;
     info->n_steps = (int)P.steps.size();
     info->n_passes = P.n_pass_launches();
+    for (const PassDesc& d : P.passes) info->n_pass_steps += d.nsteps;
     info->table_bytes = P.lay.total;
     info->open_k = P.open_k;
     info->open_width = P.open_k ? std::max(P.h, 2 * P.open_k) : 0;

@@ -79,6 +79,8 @@ struct Shape {
     static constexpr int M = M_;
     static constexpr bool BOT = TYPE == P_BOT || TYPE == P_BOT_START || TYPE == P_BOT_END;
     static constexpr int NS = pass_nsteps(TYPE, M);
+    static constexpr int XM = pass_xm(TYPE, M);           // step with four variants (-1: none)
+    static constexpr int NB = 2 * NS + (XM >= 0 ? 2 : 0);  // coefficient blocks
     static constexpr int C = BOT ? 0 : TILE_BITS - M;  // tile bit of window bit 0
     static constexpr int REG0 = BOT ? 5 : 8;            // tile bit of register bit 0
     static constexpr int regpos(int t) { return (t >= REG0 && t < REG0 + REG_BITS) ? t - REG0 : -1; }
@@ -263,12 +265,14 @@ __host__ __device__ constexpr uint64_t step_kinds() {
 }
 
 // Stage the packed coefficients of every step and variant into shared memory.
+// Blocks 2 i + x: step i, variant x; blocks 2 NS + x: the four-variant
+// step's variants 2 + x (from the pass's extra StepG after its NS steps).
 template <class SH>
 __device__ __forceinline__ void stage_coefficients(const StepG* steps, float2* sc, uint32_t tid) {
     constexpr uint64_t KINDS = step_kinds<SH>();
-    for (int w = tid; w < SH::NS * 2; w += PASS_THREADS) {
-        const int i = w >> 1, x = w & 1;
-        const float2* g = steps[i].g[x];  // [c*4 + a'*2 + s]
+    for (int w = tid; w < SH::NB; w += PASS_THREADS) {
+        const int i = w < 2 * SH::NS ? w >> 1 : SH::XM, x = w & 1;
+        const float2* g = w < 2 * SH::NS ? steps[i].g[x] : steps[SH::NS].g[x];  // [c*4 + a'*2 + s]
         float2* o = sc + w * CO;
         for (int e = 0; e < CO; ++e) o[e] = make_float2(0.f, 0.f);
         const int kind = (int)((KINDS >> (2 * i)) & 3u);
@@ -348,7 +352,12 @@ __device__ __forceinline__ void apply_step(float2 (&P)[16], float2 (&Q)[16], con
     const uint32_t lane = tid & 31u;
     const float s = (I == 0) ? scale : 1.0f;
     asm volatile("" ::: "memory");  // load each step's coefficients just before it
-    const float2* cf = sc + (I * 2 + (int)((xmask >> I) & 1u)) * CO;
+    const float2* cf;
+    if constexpr (I == SH::XM) {  // variant x_a + 2 x_b
+        cf = sc + (((xmask >> XM_HIGH_BIT) & 1u) ? 2 * SH::NS : I * 2) * CO + (int)((xmask >> I) & 1u) * CO;
+    } else {
+        cf = sc + (I * 2 + (int)((xmask >> I) & 1u)) * CO;
+    }
     if constexpr (kind == KIND_L) {
         constexpr int L = SH::lanepos(T);
         static_assert(L >= 0, "lane target");
@@ -481,7 +490,7 @@ constexpr uint32_t TILE_BYTES = (uint32_t)TILE * 8u;
 
 template <int TYPE, int M>
 constexpr int pass_smem_bytes() {
-    return 1024 + PASS_STAGES * TILE * 8 + pass_nsteps(TYPE, M) * 2 * CO * 8 + 2 * PASS_STAGES * 8 + 16;
+    return 1024 + PASS_STAGES * TILE * 8 + Shape<TYPE, M>::NB * CO * 8 + 2 * PASS_STAGES * 8 + 16;
 }
 
 template <int TYPE, int M>
@@ -489,13 +498,13 @@ __global__ void __launch_bounds__(PASS_THREADS, PASS_CTAS_PER_SM)
     pass_kernel(const PassParams p, const __grid_constant__ CUtensorMap tmap) {
     using SH = Shape<TYPE, M>;
     static_assert(SH::valid(), "invalid pass shape");
-    static_assert(SH::NS <= 32, "step mask holds 32 steps");
+    static_assert(SH::NS <= XM_HIGH_BIT, "variant mask: one bit per step, bit XM_HIGH_BIT for the four-variant step");
     constexpr int NS = SH::NS;
     extern __shared__ __align__(16) uint8_t dsm[];
     uint8_t* base = dsm + ((1024u - (pass_smem_u32(dsm) & 1023u)) & 1023u);
     float2* stages = reinterpret_cast<float2*>(base);
     float2* sc = stages + PASS_STAGES * TILE;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sc + NS * 2 * CO);  // full[3], done[3]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sc + SH::NB * CO);  // full[3], done[3]
     int* s_abort = reinterpret_cast<int*>(bars + 2 * PASS_STAGES);
     const uint32_t tid = threadIdx.x;
     const uint32_t full0 = pass_smem_u32(bars), done0 = full0 + 8 * PASS_STAGES;

@@ -174,32 +174,79 @@ static bool build_passes(Plan& P, const std::vector<int>& sizes, std::vector<Pas
             type = a.win == 0 ? P_BOT_END : P_REV;
         }
         const int M = sizes[a.win];
+        const bool turn = type == P_TOP || type == P_BOT;
         d.type = type;
         d.M = M;
         d.lo = lo[a.win];
         d.step0 = st.front();
-        d.nsteps = (int)st.size();
-        // the steps must be contiguous and match the compile-time shape
-        if (d.nsteps != pass_nsteps(type, M)) return false;
+        d.pstep0 = -1;  // set once the schedule is chosen (build_pass_steps)
+        d.nsteps = pass_nsteps(type, M);
+        // the method's steps must be contiguous and match the compile-time
+        // shape; at a turn, method steps M-2 and M-1 form pass step M-2
+        if ((int)st.size() != d.nsteps + (turn ? 1 : 0)) return false;
+        for (size_t m = 0; m < st.size(); ++m)
+            if (st[m] != d.step0 + (int)m) return false;
         for (int i = 0; i < d.nsteps; ++i) {
-            if (st[i] != d.step0 + i) return false;
+            const int m = (turn && i > M - 2) ? i + 1 : i;
             const StepSpec sp = step_spec(type, M, i);
-            const int tgt = P.step_tgt[st[i]] - d.lo;
-            const int ctl = P.step_ctl[st[i]] < 0 ? -1 : P.step_ctl[st[i]] - d.lo;
+            const int tgt = P.step_tgt[st[m]] - d.lo;
+            const int ctl = P.step_ctl[st[m]] < 0 ? -1 : P.step_ctl[st[m]] - d.lo;
             if (tgt != sp.t || ctl != sp.c) return false;
+            if (turn && i == M - 2 && (P.step_tgt[st[M - 1]] - d.lo != sp.t || P.step_ctl[st[M - 1]] >= 0))
+                return false;  // the second factor: same target, no control
         }
         int nx = 0;
-        for (int i = 0; i < d.nsteps; ++i) {
-            if (P.step_xq[st[i]] >= 0) {
-                if (nx >= 2) return false;
-                d.xs_step[nx] = i;
-                d.xs_q[nx] = P.step_xq[st[i]];
-                ++nx;
+        for (size_t m = 0; m < st.size(); ++m) {
+            if (P.step_xq[st[m]] < 0) continue;
+            int bit = (turn && (int)m > M - 2) ? (int)m - 1 : (int)m;
+            if (turn && (int)m == M - 1) {  // second factor of the composed turn step
+                if (pass_xm(type, M) != M - 2) return false;
+                bit = XM_HIGH_BIT;
             }
+            if (nx >= 2) return false;
+            d.xs_step[nx] = bit;
+            d.xs_q[nx] = P.step_xq[st[m]];
+            ++nx;
         }
         out.push_back(d);
     }
     return true;
+}
+
+// The steps of every pass as its kernel runs them. A turn's two steps on
+// one target (A with control c, then B without control) become one step
+// C[c] = B.A[c], composed in FP64; at the top both depend on an output bit,
+// and the pass's entries are followed by one more holding C for x_b = 1
+// (variant x_a in g[x_a]).
+static void build_pass_steps(Plan& P) {
+    P.pass_steps.clear();
+    for (PassDesc& d : P.passes) {
+        d.pstep0 = (int)P.pass_steps.size();
+        const bool turn = d.type == P_TOP || d.type == P_BOT, top = d.type == P_TOP;
+        StepG extra;
+        for (int i = 0; i < d.nsteps; ++i) {
+            if (!(turn && i == d.M - 2)) {
+                P.pass_steps.push_back(P.steps[d.step0 + ((turn && i > d.M - 2) ? i + 1 : i)]);
+                continue;
+            }
+            const auto& A = P.steps64[d.step0 + d.M - 2];
+            const auto& B = P.steps64[d.step0 + d.M - 1];  // uncontrolled: block c = 0 serves both
+            auto C = [&](int xa, int xb, int e) {  // e = c*4 + a''*2 + s
+                const int c = e >> 2, a2 = (e >> 1) & 1, s = e & 1;
+                cd acc = 0;
+                for (int a1 = 0; a1 < 2; ++a1) acc += B[xb * 8 + a2 * 2 + a1] * A[xa * 8 + c * 4 + a1 * 2 + s];
+                return f2(acc);
+            };
+            StepG sg;
+            for (int x = 0; x < 2; ++x)
+                for (int e = 0; e < 8; ++e) {
+                    sg.g[x][e] = C(x, top ? 0 : x, e);
+                    if (top) extra.g[x][e] = C(x, 1, e);
+                }
+            P.pass_steps.push_back(sg);
+        }
+        if (pass_xm(d.type, d.M) >= 0) P.pass_steps.push_back(extra);
+    }
 }
 
 // Modelled time of a schedule in units of one HBM pass: a pass costs the
@@ -543,6 +590,7 @@ int plan_build(Plan& P, int n, int d, const uint8_t* cliff, const uint8_t* tmask
                 }
             }
         if (P.passes.empty()) { err = "no pass schedule fits these window limits"; return TB_EINVAL; }
+        build_pass_steps(P);
     }
 
     sym_alg1(n, d, &P.width, &P.log2cost);
@@ -557,6 +605,7 @@ int plan_build(Plan& P, int n, int d, const uint8_t* cliff, const uint8_t* tmask
     auto put = [&](int64_t bytes) { const int64_t o = off; off = align_up(off + bytes, 256); return o; };
     const int64_t ns = (int64_t)P.steps.size();
     L.steps = put(ns * (int64_t)sizeof(StepG));
+    L.pass_steps = put((int64_t)P.pass_steps.size() * (int64_t)sizeof(StepG));
     L.step_tgt = put(ns);
     L.step_ctl = put(ns);
     L.step_xq = put(ns * 2);
@@ -578,6 +627,7 @@ int plan_build(Plan& P, int n, int d, const uint8_t* cliff, const uint8_t* tmask
         if (bytes) std::memcpy(P.blob.data() + o, src, bytes);
     };
     cp(L.steps, P.steps.data(), P.steps.size() * sizeof(StepG));
+    cp(L.pass_steps, P.pass_steps.data(), P.pass_steps.size() * sizeof(StepG));
     cp(L.step_tgt, P.step_tgt.data(), P.step_tgt.size());
     cp(L.step_ctl, P.step_ctl.data(), P.step_ctl.size());
     cp(L.step_xq, P.step_xq.data(), P.step_xq.size() * 2);

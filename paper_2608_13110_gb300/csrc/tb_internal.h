@@ -40,6 +40,11 @@ constexpr int MID_BITS = 10;
 //             row's targets w = M-1 (no control), M-2..0 (control w+1)
 //   BOT       row turn at address bit 0: REV targets w = M-2..0, then the
 //             next (forward) row's w = 0 (no control), 1..M-1 (control w-1)
+// At a turn the last step of one row and the first step of the next act on
+// the same target and the second has no control, so the pass kernels apply
+// their product as one step (control of the first): TOP and BOT passes run
+// 2M-2 steps. The TOP product depends on the output bits of both rows
+// (four variants, pass_xm).
 //   BOT_START first window of the first absorbed row: w = 0 (no control), 1..M-1
 //   BOT_END   last window of a reversed last row: w = M-2..0
 //   TOP_END   last window of a forward last row: w = 1..M-1
@@ -55,9 +60,17 @@ enum PassType : int {
     P_TENSOR = 7   // schedule code of a dense tensor-core pass
 };
 
+// Steps of a pass as the pass kernel runs them (turn steps composed).
 __host__ __device__ constexpr int pass_nsteps(int type, int M) {
-    return type == P_TOP || type == P_BOT ? 2 * M - 1 : type == P_BOT_START ? M : M - 1;
+    return type == P_TOP || type == P_BOT ? 2 * M - 2 : type == P_BOT_START ? M : M - 1;
 }
+
+// Index of the step with four bitstring variants (the composed top turn), -1
+// if none. Its variant is x_a + 2 x_b: x_a the output bit of the forward row
+// (bit xs_step0 of the pass's variant mask), x_b that of the reversed row
+// (bit XM_HIGH_BIT).
+__host__ __device__ constexpr int pass_xm(int type, int M) { return type == P_TOP ? M - 2 : -1; }
+constexpr int XM_HIGH_BIT = 31;
 
 // One paired step: out[.., c, a', ..] = sum_s G[c][a'][s] in[.., c, s, ..] on
 // the target bit, c the control bit (ignored for uncontrolled steps). Two
@@ -71,10 +84,11 @@ struct PassDesc {
     int type;
     int M;
     int lo;        // address bit of window bit 0
-    int step0;     // first step in the device step array
-    int nsteps;
-    int xs_step[2];  // index within the pass of a bitstring-dependent step, -1 if none
-    int xs_q[2];     // the qubit whose output bit selects its variant
+    int step0;     // first step in the device step array (the method's steps)
+    int pstep0;    // first entry of the pass in the pass-step table
+    int nsteps;    // pass_nsteps(type, M)
+    int xs_step[2];  // bit of the pass's variant mask set by an output bit, -1 if none
+    int xs_q[2];     // the qubit whose output bit sets it
 };
 
 // ---- Tensor-core dense blocks (TB_PRECISION_TF32X3 / TB_PRECISION_BF16X3) --
@@ -139,6 +153,7 @@ constexpr int JOIN_SEG_CHUNKS = 4;
 // Byte offsets of the device tables inside the workspace head.
 struct TableLayout {
     int64_t steps;     // StepG[n_steps]
+    int64_t pass_steps;  // StepG[]: the steps of every pass as its kernel runs them
     int64_t step_tgt;  // int8 target bit per step
     int64_t step_ctl;  // int8 control bit per step (-1: none)
     int64_t step_xq;   // int16 qubit of the bitstring dependence (-1: none)
@@ -183,15 +198,15 @@ __host__ __device__ constexpr StepSpec step_spec(int type, int M, int i) {
     if (type == P_FWD || type == P_TOP_END) return StepSpec{i + 1, i};
     if (type == P_REV || type == P_BOT_END) return StepSpec{M - 2 - i, M - 1 - i};
     if (type == P_BOT_START) return StepSpec{i, i == 0 ? -1 : i - 1};
-    if (type == P_TOP) {
+    if (type == P_TOP) {  // step M-2: forward target M-1 composed with the reversed row's first
         if (i < M - 1) return StepSpec{i + 1, i};
-        const int j = i - (M - 1);
-        return StepSpec{M - 1 - j, j == 0 ? -1 : M - j};
+        const int j = i - (M - 1) + 1;
+        return StepSpec{M - 1 - j, M - j};
     }
-    // P_BOT
+    // P_BOT: step M-2: reversed target 0 composed with the forward row's first
     if (i < M - 1) return StepSpec{M - 2 - i, M - 1 - i};
-    const int j = i - (M - 1);
-    return StepSpec{j, j == 0 ? -1 : j - 1};
+    const int j = i - (M - 1) + 1;
+    return StepSpec{j, j - 1};
 }
 
 }  // namespace tb

@@ -29,6 +29,7 @@ struct Plan {
     std::complex<double> w(int l, int i) const { return W[(size_t)l * (n - 1) + i]; }
     // paired steps of rows 1..n-2 in execution order
     std::vector<StepG> steps;
+    std::vector<StepG> pass_steps;  // per pass, its steps as the pass kernel runs them (PassDesc::pstep0)
     std::vector<std::array<std::complex<double>, 16>> steps64;  // the same in FP64
     std::vector<int8_t> step_tgt, step_ctl;
     std::vector<int16_t> step_xq;
