@@ -358,17 +358,18 @@ def run_ours(args, rank, world, local):
 
 
 def fma_pipe_fraction(args, info, nb, h, p, clk, dev):
-    """The FP32 passes' other ceiling: 8 FMA per entry per paired step, over
-    the pass kernels' measured time, against SMs x 128 FP32 lanes x the SM
-    clock (one FMA per lane and cycle; the paired FFMA2 issues two lanes' worth
-    in two cycles). Secondary to the HBM roofline: the two floors are within
-    15 % of each other at width 32."""
+    """The FP32 passes' other ceiling: the multiply-adds the pass kernels
+    spend per entry (8 per paired step, 16 per row turn's 4x4 block: the
+    plan's pass_madds), over the pass kernels' measured time, against SMs x
+    128 FP32 lanes x the SM clock (one FMA per lane and cycle; the paired FFMA2
+    issues two lanes' worth in two cycles). Secondary to the HBM roofline: the
+    two floors are within 15 % of each other at width 32."""
     if args.precision != "fp32" or p["ms"] <= 0:
         return None
     import torch
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     mhz = clk.get("sm_max_mhz") or 2070.0
-    fma = 8.0 * nb * args.steps * info["n_steps"] * 2.0 ** h
+    fma = float(nb) * args.steps * info["pass_madds"] * 2.0 ** h
     achieved = fma / (p["ms"] / 1e3) / 1e12
     peak = sms * 128 * mhz * 1e6 / 1e12
     return {"achieved": achieved, "peak": peak, "unit": "TFMA/s", "frac": achieved / peak,

@@ -112,10 +112,11 @@ typedef struct {
     int32_t open_k;         /* open output bits of an open plan, 0 otherwise */
     int32_t open_width;     /* open plans: width of Algorithm 2's path,
                                max(h, 2k) (Proposition 2: h for k <= d/4) */
-    int32_t n_pass_steps;   /* steps the FP32 pass kernels apply per
-                               amplitude: n_steps less one per row turn (a
-                               turn's two steps on one target run as their
-                               product); 0 without passes */
+    int32_t pass_madds;     /* real multiply-adds per boundary entry that
+                               the FP32 pass kernels spend per amplitude: 8
+                               per paired step, 16 per row turn, whose four
+                               steps on two address bits run as one 4x4
+                               block; 0 without passes */
 } tb_plan_info_t;
 
 /* Create a plan (host only: no CUDA call is made): the circuit of Sec. 2.1

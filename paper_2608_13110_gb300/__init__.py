@@ -40,7 +40,7 @@ class _Info(ctypes.Structure):
                 ("boundary_bytes", ctypes.c_int64), ("n_steps", ctypes.c_int32),
                 ("n_passes", ctypes.c_int32), ("table_bytes", ctypes.c_int64),
                 ("open_k", ctypes.c_int32), ("open_width", ctypes.c_int32),
-                ("n_pass_steps", ctypes.c_int32)]
+                ("pass_madds", ctypes.c_int32)]
 
 
 _vp = ctypes.c_void_p

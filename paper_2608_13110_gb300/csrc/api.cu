@@ -543,7 +543,7 @@ int tb_plan_info(const tb_plan* plan, tb_plan_info_t* info) {
     info->boundary_bytes = (int64_t)8 << P.h;
     info->n_steps = (int)P.steps.size();
     info->n_passes = P.n_pass_launches();
-    for (const PassDesc& d : P.passes) info->n_pass_steps += d.nsteps;
+    for (const PassDesc& d : P.passes) info->pass_madds += 8 * d.nsteps + (pass_blk(d.type, d.M) >= 0 ? 8 : 0);
     info->table_bytes = P.lay.total;
     info->open_k = P.open_k;
     info->open_width = P.open_k ? std::max(P.h, 2 * P.open_k) : 0;

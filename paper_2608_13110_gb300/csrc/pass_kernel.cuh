@@ -80,6 +80,7 @@ struct Shape {
     static constexpr bool BOT = TYPE == P_BOT || TYPE == P_BOT_START || TYPE == P_BOT_END;
     static constexpr int NS = pass_nsteps(TYPE, M);
     static constexpr int XM = pass_xm(TYPE, M);           // step with four variants (-1: none)
+    static constexpr int BLK = pass_blk(TYPE, M);         // the turn's 4x4 block (-1: none)
     static constexpr int NB = 2 * NS + (XM >= 0 ? 2 : 0);  // coefficient blocks
     static constexpr int C = BOT ? 0 : TILE_BITS - M;  // tile bit of window bit 0
     static constexpr int REG0 = BOT ? 5 : 8;            // tile bit of register bit 0
@@ -93,6 +94,12 @@ struct Shape {
     static constexpr bool valid() {
         if (M < MIN_WINDOW || M > (BOT ? MAX_WINDOW : MAX_WINDOW_HIGH)) return false;
         for (int j = 0; j < NS; ++j) {
+            if (j == BLK) {  // bottom: lanes 0, 1 with control lane 2; top: registers 3, 4 with control register 2
+                if (BOT ? (lanepos(tgt(j)) != 0 || lanepos(tgt(j) + 1) != 1 || lanepos(ctl(j)) != 2)
+                        : (regpos(tgt(j)) != 3 || regpos(tgt(j) + 1) != 4 || regpos(ctl(j)) != 2))
+                    return false;
+                continue;
+            }
             if (regpos(tgt(j)) < 0 && lanepos(tgt(j)) < 0) return false;
             if (ctl(j) >= 0 && regpos(ctl(j)) < 0 && lanepos(ctl(j)) < 0) return false;
         }
@@ -163,7 +170,7 @@ struct SlotC {
 //     control (control = register bit 4)
 // ---------------------------------------------------------------------------
 constexpr int VBIT = 4;
-constexpr int KIND_F = 0, KIND_VC = 1, KIND_VT = 2, KIND_L = 3;
+constexpr int KIND_F = 0, KIND_VC = 1, KIND_VT = 2, KIND_L = 3, KIND_BL = 4, KIND_BV = 5;
 constexpr int CO = 48;  // packed coefficients per (step, variant)
 
 __device__ __forceinline__ float2 f2x(float a) { return make_float2(a, a); }
@@ -248,8 +255,57 @@ __device__ __forceinline__ void step_lane(float2 (&P)[16], float2 (&Q)[16], cons
     }
 }
 
+// out = sum of four complex products on planar pairs; cf = 12 packed
+// coefficients, [re im -im] per input.
+__device__ __forceinline__ void cmac4_planar(const float2* cf, float2 aP, float2 aQ, float2 bP, float2 bQ,
+                                             float2 cP, float2 cQ, float2 dP, float2 dQ, float2& oP,
+                                             float2& oQ) {
+    oP = fma2(cf[0], aP, fma2(cf[2], aQ, fma2(cf[3], bP, fma2(cf[5], bQ,
+         fma2(cf[6], cP, fma2(cf[8], cQ, fma2(cf[9], dP, mul2(cf[11], dQ))))))));
+    oQ = fma2(cf[0], aQ, fma2(cf[1], aP, fma2(cf[3], bQ, fma2(cf[4], bP,
+         fma2(cf[6], cQ, fma2(cf[7], cP, fma2(cf[9], dQ, mul2(cf[10], dP))))))));
+}
+
+// Turn block on lanes 0, 1 (this lane's block index r = lane & 3): out =
+// sum_d B[r][r ^ d] in(lane ^ d); c = [re im -im] of B[r][r ^ d], d = 0..3.
+__device__ __forceinline__ void step_block_lanes(float2 (&P)[16], float2 (&Q)[16], const float2 (&c)[12]) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        float2 pp[4], qp[4];
+        pp[0] = P[k]; qp[0] = Q[k];
+#pragma unroll
+        for (int d = 1; d < 4; ++d) {
+            pp[d].x = __shfl_xor_sync(0xffffffffu, P[k].x, d);
+            pp[d].y = __shfl_xor_sync(0xffffffffu, P[k].y, d);
+            qp[d].x = __shfl_xor_sync(0xffffffffu, Q[k].x, d);
+            qp[d].y = __shfl_xor_sync(0xffffffffu, Q[k].y, d);
+        }
+        cmac4_planar(c, pp[0], qp[0], pp[1], qp[1], pp[2], qp[2], pp[3], qp[3], P[k], Q[k]);
+    }
+}
+
+// Turn block on registers 3 and 4 (register 4 = the packed pair's halves),
+// control register 2: packed registers k and k | 8 (k < 8) form the block's
+// four entries; cf = the variant's 48 coefficients (24 per control value).
+__device__ __forceinline__ void step_block_regs(float2 (&P)[16], float2 (&Q)[16], const float2* cf) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        float2 cc[24];
+        load_cf(cc, cf + 24 * c, 1.0f);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            const int k0 = kk | (c << 2), k1 = k0 | 8;
+            const float2 aP = P[k0], aQ = Q[k0], bP = P[k1], bQ = Q[k1];
+            const float2 sP = swap2(aP), sQ = swap2(aQ), tP = swap2(bP), tQ = swap2(bQ);
+            cmac4_planar(cc, aP, aQ, sP, sQ, bP, bQ, tP, tQ, P[k0], Q[k0]);
+            cmac4_planar(cc + 12, aP, aQ, sP, sQ, bP, bQ, tP, tQ, P[k1], Q[k1]);
+        }
+    }
+}
+
 template <class SH>
 __host__ __device__ constexpr int step_kind(int i) {
+    if (i == SH::BLK) return SH::BOT ? KIND_BL : KIND_BV;
     const int K = SH::regpos(SH::tgt(i));
     if (K < 0) return KIND_L;
     if (K == VBIT) return KIND_VT;
@@ -260,22 +316,57 @@ __host__ __device__ constexpr int step_kind(int i) {
 template <class SH>
 __host__ __device__ constexpr uint64_t step_kinds() {
     uint64_t k = 0;
-    for (int i = 0; i < SH::NS; ++i) k |= (uint64_t)step_kind<SH>(i) << (2 * i);
+    static_assert(3 * SH::NS <= 64, "three kind bits per step");
+    for (int i = 0; i < SH::NS; ++i) k |= (uint64_t)step_kind<SH>(i) << (3 * i);
     return k;
 }
 
 // Stage the packed coefficients of every step and variant into shared memory.
 // Blocks 2 i + x: step i, variant x; blocks 2 NS + x: the four-variant
-// step's variants 2 + x (from the pass's extra StepG after its NS steps).
+// step's (the top block's) variants 2 + x. Turn blocks (raw float2[variant][c][q'][q] over
+// BLK_ENTRIES table entries):
+//   KIND_BL (lanes 0, 1; control lane 2; no output-bit dependence): blocks
+//     2 i and 2 i + 1 hold, at 12 (4 c + r), [re im -im] of B[c][r][r ^ d]
+//     for d = 0..3, broadcast (r = the lane's block index)
+//   KIND_BV (registers 3, 4; control register 2): per variant, at 24 c + 12 b
+//     (output register: block bit t = b), four packed pairs for the inputs
+//     [register t=0, swapped, register t=1, swapped]: (B[b][a], B[b+2][a+2])
+//     and (B[b][a+2], B[b+2][a]) for a = 0, 1, each as [re im -im]
 template <class SH>
 __device__ __forceinline__ void stage_coefficients(const StepG* steps, float2* sc, uint32_t tid) {
     constexpr uint64_t KINDS = step_kinds<SH>();
     for (int w = tid; w < SH::NB; w += PASS_THREADS) {
         const int i = w < 2 * SH::NS ? w >> 1 : SH::XM, x = w & 1;
-        const float2* g = w < 2 * SH::NS ? steps[i].g[x] : steps[SH::NS].g[x];  // [c*4 + a'*2 + s]
         float2* o = sc + w * CO;
         for (int e = 0; e < CO; ++e) o[e] = make_float2(0.f, 0.f);
-        const int kind = (int)((KINDS >> (2 * i)) & 3u);
+        const int kind = (int)((KINDS >> (3 * i)) & 7u);
+        if (kind == KIND_BL || kind == KIND_BV) {
+            const float2* raw = &steps[pass_entry(SH::TYPE, SH::M, i)].g[0][0];
+            auto Bq = [&](int v, int c, int r, int q) { return raw[((v * 2 + c) * 4 + r) * 4 + q]; };
+            if (kind == KIND_BL) {  // block w - 2 i = control value c
+                for (int r = 0; r < 4; ++r)
+                    for (int d = 0; d < 4; ++d) {
+                        const float2 z = Bq(0, x, r, r ^ d);
+                        o[12 * r + 3 * d + 0] = f2x(z.x);
+                        o[12 * r + 3 * d + 1] = f2x(z.y);
+                        o[12 * r + 3 * d + 2] = f2x(-z.y);
+                    }
+            } else {
+                const int v = x + (w < 2 * SH::NS ? 0 : 2);
+                for (int c = 0; c < 2; ++c)
+                    for (int b = 0; b < 2; ++b)
+                        for (int a = 0; a < 2; ++a)
+                            for (int sw = 0; sw < 2; ++sw) {
+                                const float2 lo = Bq(v, c, b, sw ? a + 2 : a), hi = Bq(v, c, b + 2, sw ? a : a + 2);
+                                float2* t = o + 24 * c + 12 * b + 6 * a + 3 * sw;
+                                t[0] = make_float2(lo.x, hi.x);
+                                t[1] = make_float2(lo.y, hi.y);
+                                t[2] = make_float2(-lo.y, -hi.y);
+                            }
+            }
+            continue;
+        }
+        const float2* g = steps[pass_entry(SH::TYPE, SH::M, i)].g[x];  // [c*4 + a'*2 + s]
         if (kind == KIND_F) {
             for (int c = 0; c < 2; ++c)
                 for (int e = 0; e < 4; ++e) {
@@ -358,7 +449,15 @@ __device__ __forceinline__ void apply_step(float2 (&P)[16], float2 (&Q)[16], con
     } else {
         cf = sc + (I * 2 + (int)((xmask >> I) & 1u)) * CO;
     }
-    if constexpr (kind == KIND_L) {
+    if constexpr (kind == KIND_BL) {
+        float2 c[12];
+        static_assert(I > 0, "the first step carries the rescale");
+        load_cf(c, sc + (I * 2 + (int)((lane >> 2) & 1u)) * CO + (lane & 3u) * 12u, 1.0f);  // control lane 2
+        step_block_lanes(P, Q, c);
+    } else if constexpr (kind == KIND_BV) {
+        static_assert(I > 0 && I == SH::XM, "the top block has four variants and no rescale");
+        step_block_regs(P, Q, cf);
+    } else if constexpr (kind == KIND_L) {
         constexpr int L = SH::lanepos(T);
         static_assert(L >= 0, "lane target");
         const float2* ca = cf + 24 * ((lane >> L) & 1u);

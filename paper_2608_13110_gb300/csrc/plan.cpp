@@ -174,34 +174,41 @@ static bool build_passes(Plan& P, const std::vector<int>& sizes, std::vector<Pas
             type = a.win == 0 ? P_BOT_END : P_REV;
         }
         const int M = sizes[a.win];
-        const bool turn = type == P_TOP || type == P_BOT;
+        const int B = pass_blk(type, M);  // the turn block gathers method steps B..B+3
         d.type = type;
         d.M = M;
         d.lo = lo[a.win];
         d.step0 = st.front();
         d.pstep0 = -1;  // set once the schedule is chosen (build_pass_steps)
         d.nsteps = pass_nsteps(type, M);
-        // the method's steps must be contiguous and match the compile-time
-        // shape; at a turn, method steps M-2 and M-1 form pass step M-2
-        if ((int)st.size() != d.nsteps + (turn ? 1 : 0)) return false;
+        // the method's steps must be contiguous and match the compile-time shape
+        if ((int)st.size() != d.nsteps + (B >= 0 ? 3 : 0)) return false;
         for (size_t m = 0; m < st.size(); ++m)
             if (st[m] != d.step0 + (int)m) return false;
+        auto rel = [&](int bit) { return bit < 0 ? -1 : bit - d.lo; };
         for (int i = 0; i < d.nsteps; ++i) {
-            const int m = (turn && i > M - 2) ? i + 1 : i;
             const StepSpec sp = step_spec(type, M, i);
-            const int tgt = P.step_tgt[st[m]] - d.lo;
-            const int ctl = P.step_ctl[st[m]] < 0 ? -1 : P.step_ctl[st[m]] - d.lo;
-            if (tgt != sp.t || ctl != sp.c) return false;
-            if (turn && i == M - 2 && (P.step_tgt[st[M - 1]] - d.lo != sp.t || P.step_ctl[st[M - 1]] >= 0))
-                return false;  // the second factor: same target, no control
+            if (i != B) {
+                const int m = (B >= 0 && i > B) ? i + 3 : i;
+                if (rel(P.step_tgt[st[m]]) != sp.t || rel(P.step_ctl[st[m]]) != sp.c) return false;
+                continue;
+            }
+            // block: targets in {t, t+1}; controls inside it, or sp.c for the first
+            for (int m = B; m < B + 4; ++m) {
+                const int t = rel(P.step_tgt[st[m]]), c = rel(P.step_ctl[st[m]]);
+                if (t != sp.t && t != sp.t + 1) return false;
+                const bool inside = c == sp.t || c == sp.t + 1;
+                if (m == B ? c != sp.c : !(c < 0 || inside)) return false;
+            }
         }
         int nx = 0;
         for (size_t m = 0; m < st.size(); ++m) {
             if (P.step_xq[st[m]] < 0) continue;
-            int bit = (turn && (int)m > M - 2) ? (int)m - 1 : (int)m;
-            if (turn && (int)m == M - 1) {  // second factor of the composed turn step
-                if (pass_xm(type, M) != M - 2) return false;
-                bit = XM_HIGH_BIT;
+            const bool in_blk = B >= 0 && (int)m >= B && (int)m < B + 4;
+            int bit = (B >= 0 && (int)m > B) ? (int)m - 3 : (int)m;
+            if (in_blk) {  // the block's variant: first output bit low, second high
+                if (pass_xm(type, M) != B) return false;
+                bit = (nx > 0 && d.xs_step[nx - 1] == B) ? XM_HIGH_BIT : B;
             }
             if (nx >= 2) return false;
             d.xs_step[nx] = bit;
@@ -222,30 +229,56 @@ static void build_pass_steps(Plan& P) {
     P.pass_steps.clear();
     for (PassDesc& d : P.passes) {
         d.pstep0 = (int)P.pass_steps.size();
-        const bool turn = d.type == P_TOP || d.type == P_BOT, top = d.type == P_TOP;
-        StepG extra;
+        const int B = pass_blk(d.type, d.M);
         for (int i = 0; i < d.nsteps; ++i) {
-            if (!(turn && i == d.M - 2)) {
-                P.pass_steps.push_back(P.steps[d.step0 + ((turn && i > d.M - 2) ? i + 1 : i)]);
+            if (i != B) {
+                P.pass_steps.push_back(P.steps[d.step0 + ((B >= 0 && i > B) ? i + 3 : i)]);
                 continue;
             }
-            const auto& A = P.steps64[d.step0 + d.M - 2];
-            const auto& B = P.steps64[d.step0 + d.M - 1];  // uncontrolled: block c = 0 serves both
-            auto C = [&](int xa, int xb, int e) {  // e = c*4 + a''*2 + s
-                const int c = e >> 2, a2 = (e >> 1) & 1, s = e & 1;
-                cd acc = 0;
-                for (int a1 = 0; a1 < 2; ++a1) acc += B[xb * 8 + a2 * 2 + a1] * A[xa * 8 + c * 4 + a1 * 2 + s];
-                return f2(acc);
-            };
-            StepG sg;
-            for (int x = 0; x < 2; ++x)
-                for (int e = 0; e < 8; ++e) {
-                    sg.g[x][e] = C(x, top ? 0 : x, e);
-                    if (top) extra.g[x][e] = C(x, 1, e);
+            // the block: product of method steps B..B+3 on window bits t, t+1
+            // (q = bit t + 2 bit t+1), per control value c of the first and
+            // variant v = x_a + 2 x_b (x_a: bit xs_step == B, x_b: XM_HIGH_BIT)
+            const int t = step_spec(d.type, d.M, B).t;
+            StepG blk[BLK_ENTRIES];
+            float2* out = &blk[0].g[0][0];
+            for (int v = 0; v < 4; ++v)
+                for (int c = 0; c < 2; ++c) {
+                    cd Mx[4][4];
+                    for (int r = 0; r < 4; ++r)
+                        for (int q = 0; q < 4; ++q) Mx[r][q] = r == q ? 1.0 : 0.0;
+                    for (int m = B; m < B + 4; ++m) {
+                        const int gs = d.step0 + m;
+                        const auto& G = P.steps64[gs];
+                        int x = 0;
+                        if (P.step_xq[gs] >= 0)
+                            for (int j = 0; j < 2; ++j)
+                                if (d.xs_q[j] == P.step_xq[gs] && (d.xs_step[j] == B || d.xs_step[j] == XM_HIGH_BIT))
+                                    x = d.xs_step[j] == B ? (v & 1) : (v >> 1);
+                        const int tb = P.step_tgt[gs] - d.lo - t;  // 0 or 1
+                        // control: none (-1), block bit 0 or 1, or outside the block (2)
+                        const int cw = P.step_ctl[gs] < 0 ? -1 : P.step_ctl[gs] - d.lo - t;
+                        const int cb = P.step_ctl[gs] < 0 ? -1 : (cw == 0 || cw == 1) ? cw : 2;
+                        cd S[4][4];
+                        for (int r = 0; r < 4; ++r)
+                            for (int q = 0; q < 4; ++q) {
+                                S[r][q] = 0.0;
+                                if (((r ^ q) & ~(1 << tb) & 3) != 0) continue;  // other bit unchanged
+                                const int cv = cb < 0 ? 0 : cb < 2 ? ((q >> cb) & 1) : c;
+                                S[r][q] = G[x * 8 + cv * 4 + ((r >> tb) & 1) * 2 + ((q >> tb) & 1)];
+                            }
+                        cd N[4][4];
+                        for (int r = 0; r < 4; ++r)
+                            for (int q = 0; q < 4; ++q) {
+                                N[r][q] = 0.0;
+                                for (int u = 0; u < 4; ++u) N[r][q] += S[r][u] * Mx[u][q];
+                            }
+                        std::memcpy(Mx, N, sizeof(N));
+                    }
+                    for (int r = 0; r < 4; ++r)
+                        for (int q = 0; q < 4; ++q) out[((v * 2 + c) * 4 + r) * 4 + q] = f2(Mx[r][q]);
                 }
-            P.pass_steps.push_back(sg);
+            for (int e = 0; e < BLK_ENTRIES; ++e) P.pass_steps.push_back(blk[e]);
         }
-        if (pass_xm(d.type, d.M) >= 0) P.pass_steps.push_back(extra);
     }
 }
 

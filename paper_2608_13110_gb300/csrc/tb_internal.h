@@ -40,11 +40,13 @@ constexpr int MID_BITS = 10;
 //             row's targets w = M-1 (no control), M-2..0 (control w+1)
 //   BOT       row turn at address bit 0: REV targets w = M-2..0, then the
 //             next (forward) row's w = 0 (no control), 1..M-1 (control w-1)
-// At a turn the last step of one row and the first step of the next act on
-// the same target and the second has no control, so the pass kernels apply
-// their product as one step (control of the first): TOP and BOT passes run
-// 2M-2 steps. The TOP product depends on the output bits of both rows
-// (four variants, pass_xm).
+// At a turn the last two steps of one row and the first two of the next act
+// on the two outermost window bits (BOT: bits 0, 1; TOP: bits M-2, M-1), and
+// only the first of the four has its control outside them (bit 2; bit M-3).
+// The pass kernels apply their product as one dense 4x4 block per value of
+// that control (16 instead of 32 real multiply-adds per entry): TOP and BOT
+// passes run 2M-4 steps, the block at index M-3 (pass_blk). The TOP block
+// depends on the output bits of both rows (four variants, pass_xm).
 //   BOT_START first window of the first absorbed row: w = 0 (no control), 1..M-1
 //   BOT_END   last window of a reversed last row: w = M-2..0
 //   TOP_END   last window of a forward last row: w = 1..M-1
@@ -60,17 +62,35 @@ enum PassType : int {
     P_TENSOR = 7   // schedule code of a dense tensor-core pass
 };
 
-// Steps of a pass as the pass kernel runs them (turn steps composed).
+// Steps of a pass as the pass kernel runs them (turn blocks composed).
 __host__ __device__ constexpr int pass_nsteps(int type, int M) {
-    return type == P_TOP || type == P_BOT ? 2 * M - 2 : type == P_BOT_START ? M : M - 1;
+    return type == P_TOP || type == P_BOT ? 2 * M - 4 : type == P_BOT_START ? M : M - 1;
 }
 
-// Index of the step with four bitstring variants (the composed top turn), -1
+// Index of a pass's 4x4 turn block (-1: none).
+__host__ __device__ constexpr int pass_blk(int type, int M) {
+    return type == P_TOP || type == P_BOT ? M - 3 : -1;
+}
+
+// Index of the step with four bitstring variants (the top turn's block), -1
 // if none. Its variant is x_a + 2 x_b: x_a the output bit of the forward row
 // (bit xs_step0 of the pass's variant mask), x_b that of the reversed row
 // (bit XM_HIGH_BIT).
-__host__ __device__ constexpr int pass_xm(int type, int M) { return type == P_TOP ? M - 2 : -1; }
+__host__ __device__ constexpr int pass_xm(int type, int M) { return type == P_TOP ? M - 3 : -1; }
 constexpr int XM_HIGH_BIT = 31;
+
+// A turn block in the pass-step table: BLK_ENTRIES consecutive StepG read as
+// float2[4 variants][2 control values][4 rows q'][4 columns q], block index
+// q = (bit t) + 2 (bit t+1).
+constexpr int BLK_ENTRIES = 8;
+
+// Pass-step table entry of step i of a pass.
+__host__ __device__ constexpr int pass_entry(int type, int M, int i) {
+    return pass_blk(type, M) >= 0 && i > pass_blk(type, M) ? i + BLK_ENTRIES - 1 : i;
+}
+__host__ __device__ constexpr int pass_entries(int type, int M) {
+    return pass_nsteps(type, M) + (pass_blk(type, M) >= 0 ? BLK_ENTRIES - 1 : 0);
+}
 
 // One paired step: out[.., c, a', ..] = sum_s G[c][a'][s] in[.., c, s, ..] on
 // the target bit, c the control bit (ignored for uncontrolled steps). Two
@@ -78,6 +98,7 @@ constexpr int XM_HIGH_BIT = 31;
 struct StepG {
     float2 g[2][8];  // [x variant][c*4 + a'*2 + s]
 };
+static_assert(sizeof(StepG) == 16 * sizeof(float2), "StepG entries are read as raw float2 arrays");
 
 // Host-side description of one pass (launch arguments).
 struct PassDesc {
@@ -188,7 +209,9 @@ constexpr int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 namespace tb {
 
 // Window-relative target bit t and control bit c (-1: none) of step i of a
-// pass of the given shape; the planner emits steps in exactly this order.
+// pass of the given shape; for the turn block, t is its lower bit (it acts on
+// t and t+1) and c its outside control. The planner emits steps in exactly
+// this order.
 struct StepSpec {
     int t;
     int c;
@@ -198,14 +221,16 @@ __host__ __device__ constexpr StepSpec step_spec(int type, int M, int i) {
     if (type == P_FWD || type == P_TOP_END) return StepSpec{i + 1, i};
     if (type == P_REV || type == P_BOT_END) return StepSpec{M - 2 - i, M - 1 - i};
     if (type == P_BOT_START) return StepSpec{i, i == 0 ? -1 : i - 1};
-    if (type == P_TOP) {  // step M-2: forward target M-1 composed with the reversed row's first
-        if (i < M - 1) return StepSpec{i + 1, i};
-        const int j = i - (M - 1) + 1;
-        return StepSpec{M - 1 - j, M - j};
+    if (type == P_TOP) {  // forward targets 1..M-3, block {M-2, M-1}, reversed targets M-3..0
+        if (i < M - 3) return StepSpec{i + 1, i};
+        if (i == M - 3) return StepSpec{M - 2, M - 3};
+        const int j = i - (M - 3);
+        return StepSpec{M - 2 - j, M - 1 - j};
     }
-    // P_BOT: step M-2: reversed target 0 composed with the forward row's first
-    if (i < M - 1) return StepSpec{M - 2 - i, M - 1 - i};
-    const int j = i - (M - 1) + 1;
+    // P_BOT: reversed targets M-2..2, block {0, 1}, forward targets 2..M-1
+    if (i < M - 3) return StepSpec{M - 2 - i, M - 1 - i};
+    if (i == M - 3) return StepSpec{0, 2};
+    const int j = i - (M - 3) + 1;
     return StepSpec{j, j - 1};
 }
 

@@ -108,15 +108,16 @@ def test_step_and_pass_counts(tb):
 
 
 def test_turn_steps_run_composed(tb):
-    """At each row turn (a top or bottom pass) the pass kernels apply the two
-    steps on the turn's target as one: n_pass_steps = n_steps - turns."""
+    """At each row turn (a top or bottom pass) the pass kernels apply the four
+    steps on the turn's two outermost window bits as one 4x4 block (16 real
+    multiply-adds per entry instead of 4 x 8)."""
     for n, d, kw in [(70, 64, {}), (70, 63, {}), (30, 40, {}), (13, 26, {"window_bits": 6}),
                      (20, 50, {"bottom_bits": 7, "top_bits": 5})]:
         p = tb.Plan(n, d, **kw)
         turns = sum(1 for s, _, _ in p.schedule if s in ("top", "bot"))
         assert turns > 0
-        assert p.info["n_pass_steps"] == p.info["n_steps"] - turns
-    assert tb.Plan(12, 24).info["n_pass_steps"] == 0  # one-CTA kernel: no passes
+        assert p.info["pass_madds"] == 8 * p.info["n_steps"] - 16 * turns
+    assert tb.Plan(12, 24).info["pass_madds"] == 0  # one-CTA kernel: no passes
 
 
 def test_window_options(tb):
@@ -226,8 +227,8 @@ def test_dense_schedule_options(tb):
     # dense matrices (hi and lo) are part of the plan's device tables
     fp32 = tb.Plan(70, 64).info
     # tables both forms share: the FP32 form's less its pass-step table (128 B
-    # per step, at most one extra entry per pass)
-    base = fp32["table_bytes"] - 128 * (fp32["n_pass_steps"] + fp32["n_passes"]) - 256
+    # per entry: at most one per step plus a turn block's 8 per pass)
+    base = fp32["table_bytes"] - 128 * (fp32["n_steps"] + 8 * fp32["n_passes"]) - 256
     assert tb.Plan(70, 64, precision="bf16x3").info["table_bytes"] >= base + 375 * 2 * 128 * 128 * 2
     assert tb.Plan(70, 64, precision="tf32x3").info["table_bytes"] >= base + 443 * 2 * 64 * 64 * 4
 
