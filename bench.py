@@ -174,11 +174,13 @@ def cpu_baseline(seconds_cap: float = 30.0, threads: int = 0) -> dict:
 # --------------------------------------------------------------------- traffic
 def kernel_code_hash() -> str:
     """First 16 hex digits of the SHA-256 of the pass kernel's code: the
-    source of pass_kernel.cuh with its comments and all white space removed,
-    so that an edit of a comment keeps the key and any code change breaks it."""
+    sources of pass_kernel.cuh and tb_internal.h (pass shapes, launch
+    constants) with their comments and all white space removed, so that an
+    edit of a comment keeps the key and any code change breaks it."""
     import hashlib
     import re
-    src = open(os.path.join(ROOT, "paper_2608_13110_gb300", "csrc", "pass_kernel.cuh")).read()
+    csrc = os.path.join(ROOT, "paper_2608_13110_gb300", "csrc")
+    src = "".join(open(os.path.join(csrc, f)).read() for f in ("pass_kernel.cuh", "tb_internal.h"))
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     src = re.sub(r"//[^\n]*", "", src)
     src = re.sub(r"\s+", "", src)
