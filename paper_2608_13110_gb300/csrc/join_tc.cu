@@ -17,18 +17,20 @@
 // of JOIN_SEG_CHUNKS K chunks accumulates in its own tensor-memory sum (two,
 // alternating) and the segments are added in FP32 registers, round to nearest.
 //
-// One CTA per SM (128 threads, persistent). A work item is 128 rows x NT
-// output columns: thread i owns row i (tensor-memory lane i). Per K chunk of
-// JOIN_KC reals: thread 0 copies the Bm block (hi, lo) of the chunk two ahead
-// into one of four shared stages with one bulk copy; every thread splits its
-// row's JOIN_KC floats (loaded one chunk ahead) and writes A_hi / A_lo into
-// one of four tensor-memory stages;
-// thread 0 issues 3 x 4 MMAs (M = 128, N = NT, K = 8) into the segment's sum
-// and commits them to the stage's mbarrier, so the next chunk's loads run
-// while they execute. When a segment's first chunk has been issued, every
-// thread adds the previous segment's sum (its row) into its registers. The
-// epilogue writes the row sums to Z out of place (the input rows are needed
-// by the item's other N tiles).
+// One CTA per SM (persistent): 4 row warps, an MMA warp and a copy warp. A
+// work item is 128 rows x NT output columns: row thread i owns row i
+// (tensor-memory lane i). Per K chunk of JOIN_KC reals, in one of four
+// stages: the copy thread brings the chunk's Bm block (hi, lo; one bulk copy)
+// and the item's 128 x JOIN_KC A tile (one tensor copy) into shared memory as
+// soon as the stage's previous MMAs have finished; every row thread splits
+// its row's JOIN_KC floats and writes A_hi / A_lo into the stage's tensor
+// memory; the MMA thread, once both are in place, issues 3 x 4 MMAs (M = 128,
+// N = NT, K = 8) into the segment's sum and commits them to the stage's
+// mbarrier. The three roles meet only at mbarriers, so copies, splits and
+// MMAs of different chunks overlap. When a segment's first chunk has been
+// split, the rows add the previous segment's sum (their row) into their
+// registers. The epilogue writes the row sums to Z out of place (the input
+// rows are needed by the item's other N tiles).
 //
 // Every wait is bounded; a give-up is counted in the fault word, the CTA
 // stops together (__syncthreads_or), waits (bounded) for its last bulk copy
@@ -48,11 +50,10 @@ namespace {
 using namespace tcx;
 
 constexpr int JT_ROWS = 128;      // row warps 0..3: thread i owns row i (tensor-memory lane i)
-constexpr int JT_THREADS = JT_ROWS + 32;  // + the MMA warp
+constexpr int JT_THREADS = JT_ROWS + 64;  // + the MMA warp + the copy warp
 constexpr uint32_t JT_WAIT_TRIES = 1u << 22;
 constexpr uint32_t JT_TMEM_COLS = 512;
 constexpr int JT_STAGES = 4;         // B blocks in shared memory, A splits in tensor memory
-constexpr int JT_AHEAD = 2;          // B copies issued this many chunks ahead of the MMAs
 constexpr uint32_t JT_A_COL = 256;  // A stage s: hi at 256 + 64 s, lo at 256 + 64 s + 32
 // segment sums: columns [0, NT) and [NT, 2 NT), NT <= 128
 constexpr int JT_MIN_SMEM = 120 * 1024;  // more than half the SM: one CTA per SM (it holds 512 columns)
@@ -140,46 +141,57 @@ __global__ void __launch_bounds__(JT_THREADS, 1)
     };
 
     __shared__ int s_held;
-    if (warp == JT_ROWS / 32) {
-        // ------------------------------------------------ MMA warp (lane 0)
+    if (warp == JT_ROWS / 32 + 1) {
+        // ------------------------------------------------ copy warp (lane 0)
+        // Chunk cc's B block and A tile go to stage cc % S once the MMAs of
+        // chunk cc - S (the stage's previous reader, with the rows' A split in
+        // tensor memory) have finished; copies run ahead as far as that allows.
         if ((tid & 31) == 0) {
-        uint32_t c = 0, g = 0;
-        int64_t last_commit = -1;
-        bool loaded[JT_STAGES];     // a copy issued into the stage and not yet consumed
+        uint32_t c = 0;
+        bool loaded[JT_STAGES];  // a copy was issued into the stage
         uint32_t load_par[JT_STAGES];
         for (int s = 0; s < JT_STAGES; ++s) { loaded[s] = false; load_par[s] = 0; }
-        for (int64_t it = blockIdx.x; it < items && !stopped(); it += gridDim.x) {
+        bool ok = true;
+        for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x) {
             const int nt = (int)(it % ntn);
-            // B copies run JT_AHEAD chunks ahead of the MMAs (within the item); the
-            // stage a copy reuses was last read by the MMAs of the chunk
-            // JT_STAGES before it, two chunks older than the ones in flight
             const int arow0 = (int)((it / ntn) * 128);  // first row of the item (batch elements are contiguous)
-            auto issue = [&](int kc) -> bool {
+            for (int kc = 0; kc < nkc && ok; ++kc) {
                 const uint32_t cc = c + kc, s = stage_of(cc);
-                // the stage was last used by chunk cc - S: its MMAs (and so the
-                // rows' reads of its A tile) must be done
-                if (cc >= JT_STAGES && !mbar_wait(mdone0 + 8 * s, par_of(cc - JT_STAGES), JT_WAIT_TRIES)) return false;
+                if (cc >= JT_STAGES) ok = mbar_wait(mdone0 + 8 * s, par_of(cc - JT_STAGES), JT_WAIT_TRIES);
+                if (ok && stopped()) ok = false;
+                if (!ok) break;
                 expect_tx(bfull0 + 8 * s, STG);
                 bulk_load(sB0 + s * STG, p.Es + ((int64_t)nt * nkc + kc) * BLK, BLK, bfull0 + 8 * s);
                 tma_load_2d(sB0 + s * STG + BLK, &amap, kc * JOIN_KC, arow0, bfull0 + 8 * s);
                 loaded[s] = true;
                 load_par[s] = par_of(cc);
-                return true;
-            };
-            bool ok = true;
-            for (int kc = 0; kc < JT_AHEAD && kc < nkc && ok; ++kc) ok = issue(kc);
-            for (int kc = 0; kc < nkc && ok; ++kc) {
+            }
+            c += nkc;
+        }
+        if (!ok) give_up();
+        // the copies issued must land before the CTA's shared memory goes (only
+        // this thread arms b_full, so each stage's latest phase is its last copy)
+        for (int s = 0; s < JT_STAGES; ++s)
+            if (loaded[s]) (void)mbar_wait(bfull0 + 8 * s, load_par[s], JT_WAIT_TRIES);
+        }
+        __syncwarp();
+    } else if (warp == JT_ROWS / 32) {
+        // ------------------------------------------------ MMA warp (lane 0)
+        if ((tid & 31) == 0) {
+        uint32_t c = 0, g = 0;
+        int64_t last_commit = -1;
+        bool ok = true;
+        for (int64_t it = blockIdx.x; it < items && ok && !stopped(); it += gridDim.x) {
+            for (int kc = 0; kc < nkc; ++kc) {
                 const uint32_t cc = c + kc, s = stage_of(cc);
-                if (kc + JT_AHEAD < nkc) ok = issue(kc + JT_AHEAD);
                 const int sg = kc / JOIN_SEG_CHUNKS;
                 const uint32_t gg = g + sg;
                 const bool first = kc % JOIN_SEG_CHUNKS == 0;
                 // a segment's first MMA overwrites D[gg % 2], last read for segment gg - 2
-                if (ok && first && gg >= 2) ok = mbar_wait(dfree0 + 8 * (gg & 1u), ((gg - 2) >> 1) & 1u, JT_WAIT_TRIES);
+                if (first && gg >= 2) ok = mbar_wait(dfree0 + 8 * (gg & 1u), ((gg - 2) >> 1) & 1u, JT_WAIT_TRIES);
                 if (ok) ok = mbar_wait(bfull0 + 8 * s, par_of(cc), JT_WAIT_TRIES);
                 if (ok) ok = mbar_wait(afull0 + 8 * s, par_of(cc), JT_WAIT_TRIES);
                 if (!ok) break;
-                loaded[s] = false;
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(NT * (gg & 1u));
                 const uint32_t bh = sB0 + s * STG, bl = bh + PART;
@@ -196,17 +208,11 @@ __global__ void __launch_bounds__(JT_THREADS, 1)
                 mma_commit(mdone0 + 8 * s);
                 last_commit = cc;
             }
-            if (!ok) {
-                give_up();
-                break;
-            }
             c += nkc;
             g += nseg;
         }
-        // exit: the copies issued must land, and the MMAs must finish before
-        // the tensor memory can be freed
-        for (int s = 0; s < JT_STAGES; ++s)
-            if (loaded[s]) (void)mbar_wait(bfull0 + 8 * s, load_par[s], JT_WAIT_TRIES);
+        if (!ok) give_up();
+        // the MMAs must finish before the tensor memory can be freed
         bool held = false;
         if (last_commit >= 0 &&
             !mbar_wait(mdone0 + 8 * stage_of((uint32_t)last_commit), par_of((uint32_t)last_commit), JT_WAIT_TRIES))
