@@ -81,6 +81,18 @@ def test_pass_schedule_vs_state_vector(tb, oracle_mod, n, d, wb, bb, tt):
     assert rel_l2(plan.amplitudes(c.bits), ref) < TOL
 
 
+@pytest.mark.parametrize("n,d,wb,bb,tt", PASS_CASES[:10])
+def test_every_pass_shape_random_unitaries(tb, oracle_mod, n, d, wb, bb, tt):
+    """Haar one-qubit gates on every slot: the turn passes' composed 4x4 blocks
+    and every other step with dense, unstructured coefficients."""
+    u = W.random_unitaries(n, d, 7 * n + d + 100 * wb + 10 * bb + tt)
+    extra = [(q, t, u[t, q]) for t in range(d + 1) for q in range(n)]
+    plan = tb.Plan(n, d, extra=extra, window_bits=wb, bottom_bits=bb, top_bits=tt)
+    assert plan.info["n_passes"] > 0
+    bits = np.random.default_rng(n + d).integers(0, 2, size=(24, n), dtype=np.uint8)
+    assert rel_l2(plan.amplitudes(bits), oracle_mod.sv_amplitudes(n, d, u, bits)) < TOL
+
+
 @pytest.mark.parametrize("n,d", [(8, 30), (11, 28)])
 def test_pass_schedule_random_unitaries(tb, oracle_mod, n, d):
     u = W.random_unitaries(n, d, 3 * n + d)
