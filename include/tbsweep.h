@@ -46,7 +46,7 @@ enum tb_status {
     TB_OK = 0,
     TB_EINVAL = 1,   /* NULL pointer, bit not in {0,1}, Clifford index > 23, bad size */
     TB_EDOMAIN = 2,  /* circuit outside what this build contracts: n < 2, d < 2,
-                        ceil(d/2) > 40 for a plan, > 33 for evaluation */
+                        ceil(d/2) > 40 for a plan, > 35 for evaluation */
     TB_ENOMEM = 3,   /* workspace smaller than tb_workspace_bytes() or host allocation failed */
     TB_ECUDA = 4,    /* a CUDA runtime call failed; tb_last_error() has the message */
     TB_ETIMEOUT = 5  /* a bounded device wait gave up, or a server wait timed out */
@@ -126,9 +126,10 @@ typedef struct {
  * steps of a window of address bits, and the counters W and C.
  *   n, d   : qubits and CZ layers; n >= 2, 2 <= d, ceil(d/2) <= 40 (odd or
  *            even d)
- *            (else TB_EDOMAIN). Plans wider than 33 bits (2^33 complex64 =
- *            64 GiB) only report their counters: evaluating them returns
- *            TB_EDOMAIN and tb_workspace_bytes returns -1.
+ *            (else TB_EDOMAIN). Plans wider than 35 bits (2^35 complex64 =
+ *            256 GiB, the most one GPU's HBM holds) only report their
+ *            counters: evaluating them returns TB_EDOMAIN and
+ *            tb_workspace_bytes returns -1.
  *   cliff  : (d+1)*n Clifford indices 0..23, slot-major (cliff[t*n + q]);
  *            NULL means identity everywhere.
  *   tmask  : d*n bytes in {0,1}, tmask[t*n + q] = 1 puts a T after the
@@ -154,9 +155,14 @@ TB_API int tb_plan_create(int n, int d, const uint8_t* cliff, const uint8_t* tma
  * tb_amplitudes_device, where a row of the input is the prefix
  * a = (x_0..x_(n-k-1)) (n-k bytes) and the output holds 2^k amplitudes per
  * prefix, index y = sum_j b_j 2^j with b_j the output bit of qubit n-k+j. The
- * workspace holds one boundary and half a boundary per prefix evaluated
- * concurrently (tb_workspace_bytes accounts for it). tb_amplitudes_noalloc,
- * batches and servers reject open plans (TB_EINVAL). */
+ * workspace holds two boundaries per prefix evaluated concurrently: for
+ * k >= 4 the join runs on the tensor cores and writes its product out of
+ * place. When the boundary is wider than 2^33 entries, or the plan's
+ * hbm_budget_bytes cannot hold two boundaries, the plan works in place: the
+ * join runs in FP32 over the boundary itself and each late crossing writes
+ * its output rows over its input rows (one boundary per prefix; 2^35
+ * entries = 256 GiB at most). tb_workspace_bytes accounts for either.
+ * tb_amplitudes_noalloc, batches and servers reject open plans (TB_EINVAL). */
 TB_API int tb_plan_create_open(int n, int d, const uint8_t* cliff, const uint8_t* tmask,
                                const tb_gate1q* extra, int n_extra, const tb_opts* opts, int k,
                                tb_plan** out);

@@ -2,7 +2,8 @@
 
 The planner groups the paired steps of every absorbed row into windows of
 address bits (the step-fusion depth of one HBM pass: up to 10 bits, i.e. up
-to 9 steps per window and 19 at a row turn). Which window sizes are fastest
+to 9 steps per window and 16 at a row turn, whose four turn steps run as one
+4x4 block). Which window sizes are fastest
 depends on the width, the batch of bitstrings evaluated side by side and the
 GPU, so this module times candidate schedules on the device and keeps the
 winner per (GPU, width, batch bucket) in a JSON cache.
@@ -78,7 +79,7 @@ def candidate_options(h: int, n_rows: int = 8, limit: int = 8) -> list[dict]:
                 sched = tuple(p.schedule)
                 if sched in seen:
                     continue
-                steps = [2 * m - 1 if s in ("top", "bot") else m for s, m, _ in sched]
+                steps = [2 * m - 3 if s in ("top", "bot") else m for s, m, _ in sched]  # turn blocks count twice
                 seen[sched] = ((len(sched), max(steps)), {"window_bits": wb, "bottom_bits": bb, "top_bits": tt})
     ranked = [v[1] for v in sorted(seen.values(), key=lambda kv: kv[0])]
     default = {"window_bits": 0, "bottom_bits": 0, "top_bits": 0}

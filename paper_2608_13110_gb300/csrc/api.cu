@@ -93,7 +93,12 @@ CallLayout call_layout(const Plan& P) {
     c.red_blocks = (int)std::min<int64_t>(nchunks, MAX_RED_BLOCKS);
     c.partial_bytes = P.open_k ? 0 : align_up((int64_t)c.red_blocks * 16, 256);
     c.boundary_bytes = (int64_t)8 << P.h;
-    c.second_bytes = P.open_k ? ((int64_t)8 << P.h) : 0;
+    if (P.open_k) {
+        const int64_t two = c.scale_bytes + 2 * c.boundary_bytes;
+        c.open_in_place = P.h > OPEN_OUT_OF_PLACE_MAX_H ||
+                          (P.opts.hbm_budget_bytes > 0 && P.opts.hbm_budget_bytes < two);
+        c.second_bytes = c.open_in_place ? 0 : c.boundary_bytes;
+    }
     c.per_b = c.scale_bytes + c.partial_bytes + c.boundary_bytes + c.second_bytes;
     return c;
 }
@@ -339,9 +344,12 @@ int run_device(const Plan& P, const uint8_t* d_bits, int64_t nb, void* d_ws, int
 
         if (P.open_k) {  // Algorithm 2: join, late crossings, FP64 output
             const int k = P.open_k;
-            float2* second = boundary + (int64_t)batch * b_stride;  // one 2^h buffer per element
+            // out of place: one second 2^h buffer per element after the boundaries;
+            // in place: none (the join overwrites the boundary, late crossing i
+            // writes output row r' over its input row 2r': rows at stride 2^(i+1))
+            float2* second = c.open_in_place ? boundary : boundary + (int64_t)batch * b_stride;
             float2* cur = boundary;
-            if (k >= JOIN_TC_MIN_K) {  // tensor cores, out of place into the second buffer
+            if (k >= JOIN_TC_MIN_K && !c.open_in_place) {  // tensor cores, out of place into the second buffer
                 JoinTcParams jp;
                 jp.in = reinterpret_cast<const float*>(boundary);
                 jp.in_stride = b_stride;
@@ -381,12 +389,14 @@ int run_device(const Plan& P, const uint8_t* d_bits, int64_t nb, void* d_ws, int
             }
             const OpenOp* ops = tab<OpenOp>(d_ws, L.open_ops);
             for (int i = 0; i + 1 < (int)P.open_seg.size(); ++i) {
-                float2* nxt = cur == boundary ? second : boundary;
+                float2* nxt = c.open_in_place ? boundary : (cur == boundary ? second : boundary);
                 LateParams lp;
                 lp.in = cur;
                 lp.in_stride = b_stride;
                 lp.out = nxt;
                 lp.out_stride = b_stride;
+                lp.in_shift = c.open_in_place ? i : 0;
+                lp.out_shift = c.open_in_place ? i + 1 : 0;
                 lp.out_entries = (int64_t)1 << (P.h - 1 - i);
                 lp.nbatch = nbat;
                 lp.k = k;
@@ -590,7 +600,7 @@ int64_t tb_workspace_min_bytes(const tb_plan* plan) {
 int tb_plan_upload(const tb_plan* plan, void* d_ws, int64_t ws_bytes, void* stream) {
     if (!plan || !d_ws) return fail(TB_EINVAL, "NULL argument");
     const Plan& P = plan->p;
-    if (P.h > MAX_H) return fail(TB_EDOMAIN, "boundary wider than 2^33 entries");
+    if (P.h > MAX_H) return fail(TB_EDOMAIN, "boundary wider than 2^35 entries");
     if (ws_bytes < P.lay.total) return fail(TB_ENOMEM, "workspace smaller than the plan's tables");
     TB_CUDA(cudaMemcpyAsync(d_ws, P.blob.data(), (size_t)P.lay.total, cudaMemcpyHostToDevice,
                             static_cast<cudaStream_t>(stream)));
@@ -602,7 +612,7 @@ int tb_amplitudes_device(const tb_plan* plan, const uint8_t* d_bits, int64_t nb,
     if (!plan || !d_ws || (nb > 0 && (!d_bits || !d_out)) || nb < 0)
         return fail(TB_EINVAL, "NULL or negative argument");
     const Plan& P = plan->p;
-    if (P.h > MAX_H) return fail(TB_EDOMAIN, "boundary wider than 2^33 entries");
+    if (P.h > MAX_H) return fail(TB_EDOMAIN, "boundary wider than 2^35 entries");
     if (nb == 0) return TB_OK;
     if (ws_bytes < P.lay.total) return fail(TB_ENOMEM, "workspace smaller than the plan's tables");
     return run_device(P, d_bits, nb, d_ws, ws_bytes, P.lay.total, d_out, static_cast<cudaStream_t>(stream));
@@ -613,7 +623,7 @@ int tb_amplitudes(const tb_plan* plan, const uint8_t* bits, int64_t nb, void* d_
     if (!plan || !d_ws || nb < 0 || (nb > 0 && (!bits || !out)))
         return fail(TB_EINVAL, "NULL or negative argument");
     const Plan& P = plan->p;
-    if (P.h > MAX_H) return fail(TB_EDOMAIN, "boundary wider than 2^33 entries");
+    if (P.h > MAX_H) return fail(TB_EDOMAIN, "boundary wider than 2^35 entries");
     if (nb == 0) return TB_OK;
     for (int64_t i = 0; i < nb * in_row(P); ++i)
         if (bits[i] > 1) return fail(TB_EINVAL, "bitstring entries must be 0 or 1");
@@ -738,7 +748,7 @@ int tb_amplitudes_noalloc(const tb_plan* plan, const uint8_t* d_bits, int64_t nb
                           void* stream) {
     if (!plan || nb < 0 || (nb > 0 && (!d_bits || !d_out))) return fail(TB_EINVAL, "NULL or negative argument");
     const Plan& P = plan->p;
-    if (P.h > MAX_H) return fail(TB_EDOMAIN, "boundary wider than 2^33 entries");
+    if (P.h > MAX_H) return fail(TB_EDOMAIN, "boundary wider than 2^35 entries");
     if (P.open_k) return fail(TB_EINVAL, "open plans are evaluated by tb_amplitudes / tb_amplitudes_device");
     const int64_t need = P.lay.total + call_layout(P).per_b;
     if (need > NOALLOC_SCRATCH_BYTES)

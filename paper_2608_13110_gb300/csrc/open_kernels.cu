@@ -78,7 +78,11 @@ __global__ void __launch_bounds__(256, 2) join_kernel(const JoinParams p) {
 }
 
 // One late crossing: out[r'][y] = seg( in[2r'][y] + w^(y_0) in[2r'+1][y] ),
-// w = -1 for CZ (diag(1, 1, 1, w) in general).
+// w = -1 for CZ (diag(1, 1, 1, w) in general). Rows are 2^k entries at a
+// stride of 2^(k + shift) entries; in place (out == in, out_shift = in_shift
+// + 1) output row r' overwrites input row 2r', which only the CTA that reads
+// rows 2r' and 2r'+1 touches, after it has read them (a chunk is read whole
+// into shared memory before it is written back).
 // A CTA works on chunks of 2^OPEN_CHUNK_BITS output entries (or one row when
 // 2^k is larger) in shared memory; the segment's operations act on chunk
 // index bits 0..k-1.
@@ -104,8 +108,8 @@ __global__ void __launch_bounds__(256) late_kernel(const LateParams p) {
             const int64_t o = o0 + e;
             const int64_t rp = o >> p.k;
             const int y = (int)(o & (NY - 1));
-            const float2 a = in[((2 * rp) << p.k) + y];
-            const float2 c = in[((2 * rp + 1) << p.k) + y];
+            const float2 a = in[((2 * rp) << (p.k + p.in_shift)) + y];
+            const float2 c = in[((2 * rp + 1) << (p.k + p.in_shift)) + y];
             const float2 wc = (y & 1) ? make_float2(c.x * p.w.x - c.y * p.w.y, c.x * p.w.y + c.y * p.w.x) : c;
             v[e] = make_float2(a.x + wc.x, a.y + wc.y);
         }
@@ -132,7 +136,10 @@ __global__ void __launch_bounds__(256) late_kernel(const LateParams p) {
             }
             __syncthreads();
         }
-        for (int e = tid; e < len; e += 256) out[o0 + e] = v[e];
+        for (int e = tid; e < len; e += 256) {
+            const int64_t o = o0 + e;
+            out[((o >> p.k) << (p.k + p.out_shift)) + (o & (NY - 1))] = v[e];
+        }
     }
 }
 

@@ -20,11 +20,13 @@ struct JoinParams {
 };
 
 struct LateParams {
-    const float2* in;      // 2 * out_entries entries per batch element
+    const float2* in;      // 2 * out_entries / 2^k input rows per batch element
     int64_t in_stride;
-    float2* out;           // out_entries entries per batch element
+    float2* out;           // out_entries / 2^k output rows per batch element
     int64_t out_stride;
     int64_t out_entries;
+    int in_shift, out_shift;  // row r starts at entry r << (k + shift): in place, output
+                              // row r' lands on input row 2r' (out_shift = in_shift + 1)
     int nbatch;
     int k;
     const OpenOp* ops;     // the segment after this crossing

@@ -24,7 +24,11 @@ constexpr int MAX_WINDOW_HIGH = TILE_BITS - 4;  // other windows keep >= 16 cons
 // whole sweep (one CTA per bitstring).
 constexpr int SMALL_H_MAX = 12;
 constexpr int SMALL_THREADS = 256;
-constexpr int MAX_H = 33;        // widest boundary the device path evaluates
+constexpr int MAX_H = 35;        // widest boundary the device path evaluates (2^35 complex64 = 256 GiB)
+// Widest open plan whose join runs out of place into a second boundary-size
+// buffer (tensor cores, k >= JOIN_TC_MIN_K); wider open plans, and open plans
+// whose HBM budget cannot hold the second buffer, join and cross in place.
+constexpr int OPEN_OUT_OF_PLACE_MAX_H = 33;
 constexpr int MAX_PLAN_H = 40;   // widest circuit the planner accepts (counters only beyond MAX_H)
 
 // Split of the boundary address bits used by the row-0 writer and the last

@@ -29,7 +29,8 @@ struct CallLayout {
     int red_blocks = 0;          // reduction blocks
     int64_t partial_bytes = 0;   // reduction partial sums
     int64_t boundary_bytes = 0;  // the boundary, 8 * 2^h
-    int64_t second_bytes = 0;    // open plans: second buffer (join output, late ping-pong), 8 * 2^h
+    int64_t second_bytes = 0;    // open plans out of place: second buffer (join output, late ping-pong), 8 * 2^h
+    bool open_in_place = false;  // open plans in place: FP32 join, late crossings over strided rows
     int64_t per_b = 0;
 };
 

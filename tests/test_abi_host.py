@@ -250,6 +250,21 @@ def test_open_plan_domain_and_width(tb):
     assert tb._lib.tb_plan_create_open(16, 26, None, None, None, 0, None, 0, ctypes.byref(h)) == tb.TB_EDOMAIN
 
 
+def test_open_plan_workspace_in_place_or_out_of_place(tb):
+    """Open plans hold two boundaries per prefix (the tensor-core join writes
+    out of place) unless the boundary is wider than 2^33 entries or the HBM
+    budget cannot hold two; then one (join and late crossings in place)."""
+    h = 20
+    two = tb.Plan(30, 40, open_k=8).workspace_bytes(1)
+    one = tb.Plan(30, 40, open_k=8, hbm_budget_bytes=12 << 20).workspace_bytes(1)
+    assert two - one == 8 << h
+    assert tb.Plan(30, 40, open_k=8, hbm_budget_bytes=64 << 20).workspace_bytes(1) == two
+    w35 = tb.Plan(70, 70, open_k=8)
+    assert w35.info["boundary_bits"] == 35
+    assert (8 << 35) < w35.workspace_bytes(1) < (8 << 35) + (1 << 30)
+    assert tb._lib.tb_workspace_bytes(tb.Plan(70, 72, open_k=8)._h, 1) == -1  # 2^36 entries: counters only
+
+
 def test_open_plan_sweeps_only_the_fixed_region(tb):
     """The sweep absorbs rows 1..n-k-1 as middle rows: (n-k-1) h paired steps."""
     for n, d, k in [(16, 26, 3), (30, 40, 8), (70, 64, 8)]:

@@ -135,6 +135,50 @@ def test_maximum_width_33_every_suffix(tb, oracle_mod):
     assert rel_l2(got, ref) < TOL
 
 
+@pytest.mark.parametrize("k", [1, 3, 4, 6, 8, 10])
+def test_in_place_join_and_crossings(tb, oracle_mod, k):
+    """An HBM budget below two boundaries makes the plan work in place: the
+    FP32 join over the boundary itself and late crossings that write each
+    output row over its first input row (rows at doubling strides). n = 16,
+    d = 40 (width 20), three prefixes, every suffix against the state
+    vector; the in-place plan's workspace holds one boundary, not two."""
+    c = W.random_circuit(16, 40, None, 0, 4700 + k)
+    rng = np.random.default_rng(4800 + k)
+    prefixes = rng.integers(0, 2, size=(3, 16 - k), dtype=np.uint8)
+    budget = 12 << 20  # the 8 MiB boundary fits, a second one does not
+    plan = tb.Plan.from_circuit(c, open_k=k, hbm_budget_bytes=budget)
+    assert tb.Plan.from_circuit(c, open_k=k).workspace_bytes(1) - plan.workspace_bytes(1) == 8 << 20
+    got = plan.amplitudes(prefixes)
+    ref = oracle_mod.sv_amplitudes(16, 40, oracle_mod.circuit_gates(c), full_bits(prefixes, 16, k)).reshape(3, -1)
+    for i in range(3):
+        assert rel_l2(got[i], ref[i]) < TOL
+
+
+def test_maximum_width_35_in_place(tb, oracle_mod):
+    """n = d = 70, k = 8: the paper's contraction (Sec. 5: width 35, 256
+    amplitudes per prefix) on one GPU, in place (a 256 GiB boundary); every
+    suffix of a prefix against the closed form of an H / diagonal / H
+    circuit with the same T count (468)."""
+    import torch
+    from test_gpu_parity import _nonzero_bits
+    c = W.hdiag_circuit(70, 70, 468, 0, 4900)
+    k = 8
+    plan = tb.Plan.from_circuit(c, open_k=k)
+    assert plan.info["boundary_bits"] == 35
+    need = plan.workspace_bytes(1)
+    assert need < (8 << 35) + (1 << 30)  # one boundary: the plan works in place
+    torch.cuda.empty_cache()  # blocks cached by the earlier tests of this process
+    if torch.cuda.mem_get_info()[0] < need + (2 << 30):
+        pytest.skip("the device has no room for a 2^35-entry boundary")
+    prefix = _nonzero_bits(c, oracle_mod, 1, 7)[:, : c.n - k]
+    try:
+        got = plan.amplitudes(prefix)[0]
+    finally:
+        torch.cuda.empty_cache()  # hand the 256 GiB back for the tests that allocate outside PyTorch
+    ref = oracle_mod.closed_form_hdiag(c, full_bits(prefix, c.n, k))
+    assert rel_l2(got, ref) < TOL
+
+
 def test_batched_sampling_draws_from_the_conditional(tb, oracle_mod):
     """Sec. 4 sampler end to end: for every draw, the prefix is the caller's
     uniform draw and the suffix is the inverse of p(. | a) (from the FP64 state
