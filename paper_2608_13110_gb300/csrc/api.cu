@@ -95,9 +95,19 @@ CallLayout call_layout(const Plan& P) {
     c.boundary_bytes = (int64_t)8 << P.h;
     if (P.open_k) {
         const int64_t two = c.scale_bytes + 2 * c.boundary_bytes;
-        c.open_in_place = P.h > OPEN_OUT_OF_PLACE_MAX_H ||
-                          (P.opts.hbm_budget_bytes > 0 && P.opts.hbm_budget_bytes < two);
+        const int64_t budget = P.opts.hbm_budget_bytes;
+        c.open_in_place = P.h > OPEN_OUT_OF_PLACE_MAX_H || (budget > 0 && budget < two);
         c.second_bytes = c.open_in_place ? 0 : c.boundary_bytes;
+        if (c.open_in_place && P.open_k >= JOIN_TC_MIN_K) {
+            // tensor-core join in slices of rows (a multiple of its 128-row blocks)
+            const int64_t rows = (int64_t)1 << (P.h - P.open_k);
+            const int64_t slice = std::max<int64_t>(128, rows >> JOIN_SLICE_SHIFT);
+            const int64_t scratch = slice << (P.open_k + 3);
+            if (budget <= 0 || c.scale_bytes + c.boundary_bytes + scratch <= budget) {
+                c.join_slice_rows = slice;
+                c.second_bytes = scratch;
+            }
+        }
     }
     c.per_b = c.scale_bytes + c.partial_bytes + c.boundary_bytes + c.second_bytes;
     return c;
@@ -194,6 +204,23 @@ int encode_pass_map(CUtensorMap* m, const PassDesc& d, const float2* B, int h, i
     if (r != CUDA_SUCCESS)
         return fail(TB_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ") for a pass of type " +
                                   std::to_string(d.type) + ", M=" + std::to_string(d.M) + ", lo=" + std::to_string(d.lo));
+    return TB_OK;
+}
+
+// 2-D tensor map over the rows of the join's input ([rows] x [2^(k+1) floats],
+// rows of consecutive batch elements back to back), box JOIN_KC floats x 128
+// rows, 128-byte swizzle (the tensor-core join's A tiles).
+int encode_join_map(CUtensorMap* m, const float2* base, int k, int64_t rows) {
+    EncodeTiledFn enc = encode_tiled_fn();
+    if (!enc) return fail(TB_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const cuuint64_t dim[2] = {(cuuint64_t)(2 << k), (cuuint64_t)rows};
+    const cuuint64_t stride[1] = {(cuuint64_t)(2 << k) * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)JOIN_KC, 128}, estr[2] = {1, 1};
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2*>(base), dim, stride, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return fail(TB_ECUDA, "cuTensorMapEncodeTiled failed for the join (" + std::to_string((int)r) + ")");
     return TB_OK;
 }
 
@@ -345,11 +372,41 @@ int run_device(const Plan& P, const uint8_t* d_bits, int64_t nb, void* d_ws, int
         if (P.open_k) {  // Algorithm 2: join, late crossings, FP64 output
             const int k = P.open_k;
             // out of place: one second 2^h buffer per element after the boundaries;
-            // in place: none (the join overwrites the boundary, late crossing i
-            // writes output row r' over its input row 2r': rows at stride 2^(i+1))
+            // in place: the join's result replaces the boundary and late
+            // crossing i writes output row r' over its input row 2r' (rows at
+            // stride 2^(i+1)); a tensor-core join then goes through a scratch of
+            // join_slice_rows rows after the boundaries, one slice at a time
             float2* second = c.open_in_place ? boundary : boundary + (int64_t)batch * b_stride;
             float2* cur = boundary;
-            if (k >= JOIN_TC_MIN_K && !c.open_in_place) {  // tensor cores, out of place into the second buffer
+            if (c.open_in_place && c.join_slice_rows > 0) {
+                float2* scratch = boundary + (int64_t)batch * b_stride;
+                const int64_t rows = b_stride >> k;
+                for (int bb = 0; bb < nbat; ++bb)
+                    for (int64_t r0 = 0; r0 < rows; r0 += c.join_slice_rows) {
+                        float2* slice = boundary + (int64_t)bb * b_stride + (r0 << k);
+                        JoinTcParams jp;
+                        jp.in = reinterpret_cast<const float*>(slice);
+                        jp.in_stride = 0;
+                        jp.out = reinterpret_cast<float*>(scratch);
+                        jp.out_stride = 0;
+                        jp.Es = tab<uint8_t>(d_ws, L.open_Es);
+                        jp.KR = 2 << k;
+                        jp.rows = c.join_slice_rows;
+                        jp.nbatch = 1;
+                        jp.fault = fault;
+                        const int64_t items = (jp.rows / 128) * (jp.KR / join_nt(k));
+                        CUtensorMap amap;
+                        const int rc = encode_join_map(&amap, slice, k, jp.rows);
+                        if (rc != TB_OK) return rc;
+                        {
+                            ProfScope ps(PC_JOIN, 16.0 * (double)(jp.rows << k), st);
+                            TB_CUDA(launch_join_tc(k, jp, amap, (int)std::min<int64_t>(items, nsm), st));
+                        }
+                        ProfScope ps(PC_JOIN, 16.0 * (double)(jp.rows << k), st);
+                        TB_CUDA(cudaMemcpyAsync(slice, scratch, (size_t)(jp.rows << k) * sizeof(float2),
+                                                cudaMemcpyDeviceToDevice, st));
+                    }
+            } else if (k >= JOIN_TC_MIN_K && !c.open_in_place) {  // tensor cores, out of place into the second buffer
                 JoinTcParams jp;
                 jp.in = reinterpret_cast<const float*>(boundary);
                 jp.in_stride = b_stride;
@@ -362,18 +419,8 @@ int run_device(const Plan& P, const uint8_t* d_bits, int64_t nb, void* d_ws, int
                 jp.fault = fault;
                 const int64_t items = (int64_t)nbat * (jp.rows / 128) * (jp.KR / join_nt(k));
                 CUtensorMap amap;
-                {
-                    EncodeTiledFn enc = encode_tiled_fn();
-                    if (!enc) return fail(TB_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
-                    const cuuint64_t dim[2] = {(cuuint64_t)jp.KR, (cuuint64_t)(jp.rows * nbat)};
-                    const cuuint64_t stride[1] = {(cuuint64_t)jp.KR * 4};
-                    const cuuint32_t box[2] = {(cuuint32_t)JOIN_KC, 128}, estr[2] = {1, 1};
-                    const CUresult r = enc(&amap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, boundary, dim, stride, box, estr,
-                                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-                    if (r != CUDA_SUCCESS)
-                        return fail(TB_ECUDA, "cuTensorMapEncodeTiled failed for the join (" + std::to_string((int)r) + ")");
-                }
+                const int rc = encode_join_map(&amap, boundary, k, jp.rows * nbat);
+                if (rc != TB_OK) return rc;
                 ProfScope ps(PC_JOIN, 16.0 * (double)nbat * (double)b_stride, st);
                 TB_CUDA(launch_join_tc(k, jp, amap, (int)std::min<int64_t>(items, nsm), st));
                 cur = second;

@@ -29,6 +29,10 @@ constexpr int MAX_H = 35;        // widest boundary the device path evaluates (2
 // buffer (tensor cores, k >= JOIN_TC_MIN_K); wider open plans, and open plans
 // whose HBM budget cannot hold the second buffer, join and cross in place.
 constexpr int OPEN_OUT_OF_PLACE_MAX_H = 33;
+// In place, the tensor-core join runs in slices of 2^-JOIN_SLICE_SHIFT of the
+// boundary's rows (at least 128) through a scratch of one slice, each slice
+// copied back over its rows (a row's product depends on that row alone).
+constexpr int JOIN_SLICE_SHIFT = 6;
 constexpr int MAX_PLAN_H = 40;   // widest circuit the planner accepts (counters only beyond MAX_H)
 
 // Split of the boundary address bits used by the row-0 writer and the last

@@ -30,7 +30,10 @@ struct CallLayout {
     int64_t partial_bytes = 0;   // reduction partial sums
     int64_t boundary_bytes = 0;  // the boundary, 8 * 2^h
     int64_t second_bytes = 0;    // open plans out of place: second buffer (join output, late ping-pong), 8 * 2^h
-    bool open_in_place = false;  // open plans in place: FP32 join, late crossings over strided rows
+    bool open_in_place = false;  // open plans in place: late crossings over strided rows, and a join
+                                 // in row slices through second_bytes of scratch (tensor cores) or,
+                                 // when join_slice_rows is 0, in FP32 over the boundary itself
+    int64_t join_slice_rows = 0;  // in place: boundary rows per tensor-core join slice
     int64_t per_b = 0;
 };
 

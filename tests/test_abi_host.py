@@ -253,15 +253,20 @@ def test_open_plan_domain_and_width(tb):
 def test_open_plan_workspace_in_place_or_out_of_place(tb):
     """Open plans hold two boundaries per prefix (the tensor-core join writes
     out of place) unless the boundary is wider than 2^33 entries or the HBM
-    budget cannot hold two; then one (join and late crossings in place)."""
-    h = 20
-    two = tb.Plan(30, 40, open_k=8).workspace_bytes(1)
-    one = tb.Plan(30, 40, open_k=8, hbm_budget_bytes=12 << 20).workspace_bytes(1)
-    assert two - one == 8 << h
-    assert tb.Plan(30, 40, open_k=8, hbm_budget_bytes=64 << 20).workspace_bytes(1) == two
+    budget cannot hold two; then one boundary plus, for k >= 4, a scratch of
+    one join slice (2^-6 of the rows, at least 128 rows), or no scratch at
+    all (FP32 join) when the budget cannot hold that either."""
+    h, k = 20, 8
+    scratch = max(128, (1 << (h - k)) >> 6) << (k + 3)
+    two = tb.Plan(30, 40, open_k=k).workspace_bytes(1)
+    one = tb.Plan(30, 40, open_k=k, hbm_budget_bytes=12 << 20).workspace_bytes(1)
+    assert two - one == (8 << h) - scratch
+    bare = tb.Plan(30, 40, open_k=k, hbm_budget_bytes=(8 << h) + (64 << 10)).workspace_bytes(1)
+    assert one - bare == scratch
+    assert tb.Plan(30, 40, open_k=k, hbm_budget_bytes=64 << 20).workspace_bytes(1) == two
     w35 = tb.Plan(70, 70, open_k=8)
     assert w35.info["boundary_bits"] == 35
-    assert (8 << 35) < w35.workspace_bytes(1) < (8 << 35) + (1 << 30)
+    assert (8 << 35) + (4 << 30) < w35.workspace_bytes(1) < (8 << 35) + (5 << 30)  # + a 4 GiB join slice
     assert tb._lib.tb_workspace_bytes(tb.Plan(70, 72, open_k=8)._h, 1) == -1  # 2^36 entries: counters only
 
 

@@ -135,19 +135,24 @@ def test_maximum_width_33_every_suffix(tb, oracle_mod):
     assert rel_l2(got, ref) < TOL
 
 
-@pytest.mark.parametrize("k", [1, 3, 4, 6, 8, 10])
-def test_in_place_join_and_crossings(tb, oracle_mod, k):
+@pytest.mark.parametrize("k,join", [(1, "fp32"), (3, "fp32"), (4, "slices"), (4, "fp32"), (6, "slices"),
+                                    (8, "slices"), (8, "fp32"), (10, "slices"), (10, "fp32")])
+def test_in_place_join_and_crossings(tb, oracle_mod, k, join):
     """An HBM budget below two boundaries makes the plan work in place: the
-    FP32 join over the boundary itself and late crossings that write each
-    output row over its first input row (rows at doubling strides). n = 16,
-    d = 40 (width 20), three prefixes, every suffix against the state
-    vector; the in-place plan's workspace holds one boundary, not two."""
+    join in row slices on the tensor cores through a scratch of one slice
+    (or, when the budget cannot hold that, in FP32 over the boundary itself)
+    and late crossings that write each output row over its first input row
+    (rows at doubling strides). n = 16, d = 40 (width 20), three prefixes,
+    every suffix against the state vector."""
     c = W.random_circuit(16, 40, None, 0, 4700 + k)
     rng = np.random.default_rng(4800 + k)
     prefixes = rng.integers(0, 2, size=(3, 16 - k), dtype=np.uint8)
-    budget = 12 << 20  # the 8 MiB boundary fits, a second one does not
+    # 12 MiB: the 8 MiB boundary and a join slice fit, a second boundary does
+    # not; 8 MiB + 64 KiB: the boundary and the rescaling state only
+    budget = (12 << 20) if join == "slices" else (8 << 20) + (64 << 10)
     plan = tb.Plan.from_circuit(c, open_k=k, hbm_budget_bytes=budget)
-    assert tb.Plan.from_circuit(c, open_k=k).workspace_bytes(1) - plan.workspace_bytes(1) == 8 << 20
+    scratch = (max(128, (1 << (20 - k)) >> 6) << (k + 3)) if join == "slices" else 0
+    assert tb.Plan.from_circuit(c, open_k=k).workspace_bytes(1) - plan.workspace_bytes(1) == (8 << 20) - scratch
     got = plan.amplitudes(prefixes)
     ref = oracle_mod.sv_amplitudes(16, 40, oracle_mod.circuit_gates(c), full_bits(prefixes, 16, k)).reshape(3, -1)
     for i in range(3):
@@ -166,7 +171,7 @@ def test_maximum_width_35_in_place(tb, oracle_mod):
     plan = tb.Plan.from_circuit(c, open_k=k)
     assert plan.info["boundary_bits"] == 35
     need = plan.workspace_bytes(1)
-    assert need < (8 << 35) + (1 << 30)  # one boundary: the plan works in place
+    assert need < (8 << 35) + (5 << 30)  # one boundary and a 4 GiB join slice: the plan works in place
     torch.cuda.empty_cache()  # blocks cached by the earlier tests of this process
     if torch.cuda.mem_get_info()[0] < need + (2 << 30):
         pytest.skip("the device has no room for a 2^35-entry boundary")
