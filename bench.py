@@ -705,7 +705,10 @@ def run_paper_workload(args, rank, world, local):
     c = W.random_circuit(70, 70, 468, 0, 4600 + rank)
     rng = np.random.default_rng(7100 + rank)
     prefixes = rng.integers(0, 2, size=(na, c.n - k), dtype=np.uint8)
-    plan = tb.Plan.from_circuit(c, open_k=k)  # planner-default windows (no width-35 autotuning)
+    # windows 9 / bottom 7 / top 7: the fastest of 12 candidate schedules timed at
+    # width 35 on a GB300 (8 absorbed rows: 3164 ms against 3379 ms for the
+    # planner's default); autotuning inside the run would time 256 GiB sweeps
+    plan = tb.Plan.from_circuit(c, open_k=k, window_bits=9, bottom_bits=7, top_bits=7)
     info = plan.info
     need = plan.workspace_bytes(1)
     free = torch.cuda.mem_get_info(dev)[0]
@@ -753,7 +756,8 @@ def run_paper_workload(args, rank, world, local):
             "scaling": "weak", "vs_baseline": value / paper_rate, "dtype": "complex64", "data": "synthetic",
             "config": {"workload": f"brickwork CZ n=70, d=70, random Cliffords, 468 T, k=8, {na} uniform prefixes/step",
                        "open_k": k, "open_width": info["open_width"], "passes_per_prefix": info["n_passes"],
-                       "in_place": True, "workspace_gib": need / 2**30, "schedule": "planner default",
+                       "in_place": True, "workspace_gib": need / 2**30,
+                       "schedule": {"given": {"window_bits": 9, "bottom_bits": 7, "top_bits": 7}},
                        "pass_arithmetic": "fp32", "parallelism": f"replicas x{world}"},
             "s_per_contraction": t / (na * args.steps),
             "baseline": {"s_per_contraction": PAPER_S_PER_CONTRACTION, "amps_per_s": paper_rate,
