@@ -450,9 +450,8 @@ int run_device(const Plan& P, const uint8_t* d_bits, int64_t nb, void* d_ws, int
                 lp.ops = ops + P.open_seg[i];
                 lp.nops = P.open_seg[i + 1] - P.open_seg[i];
                 lp.w = P.open_w[i];
-                const int64_t chunks = ((lp.out_entries + (1 << OPEN_CHUNK_BITS) - 1) >> OPEN_CHUNK_BITS) * nbat;
                 ProfScope ps(PC_LATE, 24.0 * (double)nbat * (double)lp.out_entries, st);
-                TB_CUDA(launch_late(lp, (int)std::min<int64_t>(chunks, 8LL * nsm), st));
+                TB_CUDA(launch_late(lp, 16 * nsm, st));
                 cur = nxt;
             }
             OpenFinalParams op;

@@ -6,6 +6,8 @@
 // 0..k-1), r = the late crossing bits (address bits k..h-1, the next one to
 // be contracted lowest).
 
+#include <algorithm>
+
 #include "open_kernels.cuh"
 
 namespace tb {
@@ -80,65 +82,103 @@ __global__ void __launch_bounds__(256, 2) join_kernel(const JoinParams p) {
 // One late crossing: out[r'][y] = seg( in[2r'][y] + w^(y_0) in[2r'+1][y] ),
 // w = -1 for CZ (diag(1, 1, 1, w) in general). Rows are 2^k entries at a
 // stride of 2^(k + shift) entries; in place (out == in, out_shift = in_shift
-// + 1) output row r' overwrites input row 2r', which only the CTA that reads
-// rows 2r' and 2r'+1 touches, after it has read them (a chunk is read whole
-// into shared memory before it is written back).
-// A CTA works on chunks of 2^OPEN_CHUNK_BITS output entries (or one row when
-// 2^k is larger) in shared memory; the segment's operations act on chunk
-// index bits 0..k-1.
+// + 1) output row r' overwrites input row 2r', which only the warp that reads
+// rows 2r' and 2r'+1 touches, after it has read them.
+// One warp per output row (k >= 5: lanes hold y bits 0..4, R = 2^(k-5)
+// registers the rest) or per 2^(5-k) rows (k < 5: the lanes' high bits pick
+// the row): the segment's operations act on y, so a gate on a lane bit is a
+// shuffle and a gate on a register bit is register arithmetic; no block
+// barrier after the operations are staged.
+template <int K>
+struct LateShape {
+    static constexpr int LB = K >= 5 ? 5 : K;              // y bits on lanes
+    static constexpr int R = K >= 5 ? 1 << (K - 5) : 1;    // registers per lane
+    static constexpr int ROWS = K >= 5 ? 1 : 1 << (5 - K);  // rows per warp
+};
+
+template <int K, int JR>
+__device__ __forceinline__ void late_reg_gate(float2 (&v)[LateShape<K>::R], const float2* m) {
+    constexpr int R = LateShape<K>::R;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (r & (1 << JR)) continue;
+        const int r1 = r | (1 << JR);
+        const float2 x0 = v[r], x1 = v[r1];
+        v[r] = cmac(cmac(make_float2(0.f, 0.f), m[0], x0), m[1], x1);
+        v[r1] = cmac(cmac(make_float2(0.f, 0.f), m[2], x0), m[3], x1);
+    }
+}
+
+template <int K>
 __global__ void __launch_bounds__(256) late_kernel(const LateParams p) {
-    __shared__ float2 v[1 << OPEN_CHUNK_BITS];
+    using S = LateShape<K>;
+    constexpr int R = S::R, LB = S::LB, ROWS = S::ROWS, NRB = K - LB;  // NRB: y bits in registers
     __shared__ OpenOp ops[LATE_MAX_OPS];
-    const int tid = threadIdx.x;
-    for (int i = tid; i < p.nops; i += 256) ops[i] = p.ops[i];
-    const int NY = 1 << p.k;
-    const int chunk = NY > (1 << OPEN_CHUNK_BITS) ? NY : (1 << OPEN_CHUNK_BITS);  // k <= 10: 1024
-    const int64_t per_b = p.out_entries;  // output entries per batch element
-    const int64_t chunks_per_b = (per_b + chunk - 1) / chunk;
-    const int64_t nchunks = chunks_per_b * p.nbatch;
+    for (int i = threadIdx.x; i < p.nops; i += blockDim.x) ops[i] = p.ops[i];
     __syncthreads();
-    for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-        const int64_t b = ch / chunks_per_b;
-        const int64_t o0 = (ch - b * chunks_per_b) * chunk;  // first output entry
-        const int len = (int)((per_b - o0) < chunk ? (per_b - o0) : chunk);
+    const int lane = threadIdx.x & 31;
+    const int yl = lane & ((1 << LB) - 1);  // this lane's y bits 0..LB-1
+    const int rsub = lane >> LB;            // row within the warp's group (k < 5)
+    const int64_t rows_out = p.out_entries >> K;
+    const int64_t groups_per_b = (rows_out + ROWS - 1) / ROWS;
+    const int64_t ngroups = groups_per_b * p.nbatch;
+    const int64_t wstep = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t gi = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); gi < ngroups; gi += wstep) {
+        const int64_t b = gi / groups_per_b;
+        const int64_t rp = (gi - b * groups_per_b) * ROWS + rsub;
+        const bool valid = rp < rows_out;
         const float2* in = p.in + b * p.in_stride;
         float2* out = p.out + b * p.out_stride;
-        __syncthreads();
-        for (int e = tid; e < len; e += 256) {
-            const int64_t o = o0 + e;
-            const int64_t rp = o >> p.k;
-            const int y = (int)(o & (NY - 1));
-            const float2 a = in[((2 * rp) << (p.k + p.in_shift)) + y];
-            const float2 c = in[((2 * rp + 1) << (p.k + p.in_shift)) + y];
-            const float2 wc = (y & 1) ? make_float2(c.x * p.w.x - c.y * p.w.y, c.x * p.w.y + c.y * p.w.x) : c;
-            v[e] = make_float2(a.x + wc.x, a.y + wc.y);
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int y = yl | (r << LB);
+            v[r] = make_float2(0.f, 0.f);
+            if (valid) {
+                const float2 a = in[((2 * rp) << (K + p.in_shift)) + y];
+                const float2 c = in[((2 * rp + 1) << (K + p.in_shift)) + y];
+                const float2 wc = (y & 1) ? make_float2(c.x * p.w.x - c.y * p.w.y, c.x * p.w.y + c.y * p.w.x) : c;
+                v[r] = make_float2(a.x + wc.x, a.y + wc.y);
+            }
         }
-        __syncthreads();
-        for (int q = 0; q < p.nops; ++q) {
+        for (int q = 0; q < p.nops; ++q) {  // warp-uniform
             const OpenOp& op = ops[q];
+            const int j = op.j;
             if (op.kind == 0) {
-                const int half = len >> 1;
-                for (int e = tid; e < half; e += 256) {
-                    const int lo = ((e >> op.j) << (op.j + 1)) | (e & ((1 << op.j) - 1));
-                    const int hi = lo | (1 << op.j);
-                    const float2 x0 = v[lo], x1 = v[hi];
-                    float2 r0 = make_float2(0.f, 0.f), r1 = make_float2(0.f, 0.f);
-                    r0 = cmac(cmac(r0, op.m[0], x0), op.m[1], x1);
-                    r1 = cmac(cmac(r1, op.m[2], x0), op.m[3], x1);
-                    v[lo] = r0;
-                    v[hi] = r1;
+                if (j < LB) {  // partner lane = lane ^ 2^j
+                    const int a = (yl >> j) & 1;
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        float2 t;
+                        t.x = __shfl_xor_sync(0xffffffffu, v[r].x, 1 << j);
+                        t.y = __shfl_xor_sync(0xffffffffu, v[r].y, 1 << j);
+                        // lo lane: m0 own + m1 partner; hi lane: m2 partner + m3 own
+                        v[r] = a ? cmac(cmac(make_float2(0.f, 0.f), op.m[2], t), op.m[3], v[r])
+                                 : cmac(cmac(make_float2(0.f, 0.f), op.m[0], v[r]), op.m[1], t);
+                    }
+                } else if constexpr (NRB > 0) {
+                    switch (j - LB) {
+                        case 0: late_reg_gate<K, 0>(v, op.m); break;
+                        case 1: if constexpr (NRB > 1) late_reg_gate<K, 1>(v, op.m); break;
+                        case 2: if constexpr (NRB > 2) late_reg_gate<K, 2>(v, op.m); break;
+                        case 3: if constexpr (NRB > 3) late_reg_gate<K, 3>(v, op.m); break;
+                        case 4: if constexpr (NRB > 4) late_reg_gate<K, 4>(v, op.m); break;
+                        default: break;
+                    }
                 }
             } else {  // entangler diag(1, 1, 1, m[0]) on bits j, j+1
                 const float2 w = op.m[0];
-                for (int e = tid; e < len; e += 256)
-                    if (((e >> op.j) & 1) && ((e >> (op.j + 1)) & 1))
-                        v[e] = make_float2(v[e].x * w.x - v[e].y * w.y, v[e].x * w.y + v[e].y * w.x);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int y = yl | (r << LB);
+                    if (((y >> j) & 1) && ((y >> (j + 1)) & 1))
+                        v[r] = make_float2(v[r].x * w.x - v[r].y * w.y, v[r].x * w.y + v[r].y * w.x);
+                }
             }
-            __syncthreads();
         }
-        for (int e = tid; e < len; e += 256) {
-            const int64_t o = o0 + e;
-            out[((o >> p.k) << (p.k + p.out_shift)) + (o & (NY - 1))] = v[e];
+        if (valid) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) out[(rp << (K + p.out_shift)) + (yl | (r << LB))] = v[r];
         }
     }
 }
@@ -190,10 +230,29 @@ cudaError_t launch_join(int k, const JoinParams& p, int grid, cudaStream_t st) {
     }
 }
 
-cudaError_t launch_late(const LateParams& p, int grid, cudaStream_t st) {
-    if (p.nops > LATE_MAX_OPS || p.k > OPEN_CHUNK_BITS) return cudaErrorInvalidValue;
-    late_kernel<<<grid, 256, 0, st>>>(p);
+template <int K>
+cudaError_t launch_late_k(const LateParams& p, int max_grid, cudaStream_t st) {
+    constexpr int ROWS = LateShape<K>::ROWS;
+    const int64_t groups = ((p.out_entries >> K) + ROWS - 1) / ROWS * p.nbatch;  // one warp each
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((groups + 7) / 8, max_grid));
+    late_kernel<K><<<grid, 256, 0, st>>>(p);
     return cudaGetLastError();
+}
+
+cudaError_t launch_late(const LateParams& p, int max_grid, cudaStream_t st) {
+    if (p.nops > LATE_MAX_OPS || p.k < 1 || p.k > OPEN_MAX_K) return cudaErrorInvalidValue;
+    switch (p.k) {
+        case 1: return launch_late_k<1>(p, max_grid, st);
+        case 2: return launch_late_k<2>(p, max_grid, st);
+        case 3: return launch_late_k<3>(p, max_grid, st);
+        case 4: return launch_late_k<4>(p, max_grid, st);
+        case 5: return launch_late_k<5>(p, max_grid, st);
+        case 6: return launch_late_k<6>(p, max_grid, st);
+        case 7: return launch_late_k<7>(p, max_grid, st);
+        case 8: return launch_late_k<8>(p, max_grid, st);
+        case 9: return launch_late_k<9>(p, max_grid, st);
+        default: return launch_late_k<10>(p, max_grid, st);
+    }
 }
 
 cudaError_t launch_open_finalize(const OpenFinalParams& p, int nbatch, cudaStream_t st) {

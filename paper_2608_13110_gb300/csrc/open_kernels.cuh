@@ -62,7 +62,9 @@ cudaError_t launch_join(int k, const JoinParams& p, int grid, cudaStream_t st);
 // amap: 2-D tensor map over the rows of every batch element ([rows * nbatch]
 // x [2^(k+1) floats]), box JOIN_KC floats x 128 rows, 128-byte swizzle.
 cudaError_t launch_join_tc(int k, const JoinTcParams& p, const CUtensorMap& amap, int grid, cudaStream_t st);
-cudaError_t launch_late(const LateParams& p, int grid, cudaStream_t st);
+// max_grid caps the CTAs (8 warps each, one warp per output row or per
+// 2^(5-k) rows for k < 5).
+cudaError_t launch_late(const LateParams& p, int max_grid, cudaStream_t st);
 cudaError_t launch_open_finalize(const OpenFinalParams& p, int nbatch, cudaStream_t st);
 
 }  // namespace tb

@@ -167,7 +167,6 @@ struct OpenOp {
     float2 m[4];  // row-major 2x2 (kind 0)
 };
 constexpr int OPEN_MAX_K = 10;          // 2^k x 2^k early-region matrix built on the host
-constexpr int OPEN_CHUNK_BITS = 10;     // late-region kernels work on 1024-entry chunks
 constexpr int JOIN_TILE = 8192;         // join kernel: boundary entries per CTA tile
 // Join on the tensor cores (3xTF32) for k >= JOIN_TC_MIN_K: Z = B.E as a real
 // GEMM with K = N = 2^(k+1); the split E is stored in blocks of JOIN_KC K rows
