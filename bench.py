@@ -705,10 +705,10 @@ def run_paper_workload(args, rank, world, local):
     c = W.random_circuit(70, 70, 468, 0, 4600 + rank)
     rng = np.random.default_rng(7100 + rank)
     prefixes = rng.integers(0, 2, size=(na, c.n - k), dtype=np.uint8)
-    # windows 9 / bottom 7 / top 7: the fastest of 12 candidate schedules timed at
-    # width 35 on a GB300 (8 absorbed rows: 3164 ms against 3379 ms for the
-    # planner's default); autotuning inside the run would time 256 GiB sweeps
-    plan = tb.Plan.from_circuit(c, open_k=k, window_bits=9, bottom_bits=7, top_bits=7)
+    # windows 10 / bottom 10 / top 9: the fastest of the schedules timed at width
+    # 35 on a GB300 (8 absorbed rows: 3087 ms; 9 / 7 / 7: 3156 ms; the planner's
+    # default 3217 ms); autotuning inside the run would time 256 GiB sweeps
+    plan = tb.Plan.from_circuit(c, open_k=k, window_bits=10, bottom_bits=10, top_bits=9)
     info = plan.info
     need = plan.workspace_bytes(1)
     free = torch.cuda.mem_get_info(dev)[0]
@@ -757,7 +757,7 @@ def run_paper_workload(args, rank, world, local):
             "config": {"workload": f"brickwork CZ n=70, d=70, random Cliffords, 468 T, k=8, {na} uniform prefixes/step",
                        "open_k": k, "open_width": info["open_width"], "passes_per_prefix": info["n_passes"],
                        "in_place": True, "workspace_gib": need / 2**30,
-                       "schedule": {"given": {"window_bits": 9, "bottom_bits": 7, "top_bits": 7}},
+                       "schedule": {"given": {"window_bits": 10, "bottom_bits": 10, "top_bits": 9}},
                        "pass_arithmetic": "fp32", "parallelism": f"replicas x{world}"},
             "s_per_contraction": t / (na * args.steps),
             "baseline": {"s_per_contraction": PAPER_S_PER_CONTRACTION, "amps_per_s": paper_rate,

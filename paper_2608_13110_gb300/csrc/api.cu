@@ -180,7 +180,7 @@ int encode_pass_map(CUtensorMap* m, const PassDesc& d, const float2* B, int h, i
         box[0] = 32; box[1] = 256; box[2] = 2; box[3] = 1; box[4] = 1;
     } else {
         const int M = d.M, lo = d.lo, C = TILE_BITS - M;
-        if (C < 4 || lo < C || lo + M > h) return fail(TB_EINVAL, "pass window outside the tensor-copy layout");
+        if (C < 3 || lo < C || lo + M > h) return fail(TB_EINVAL, "pass window outside the tensor-copy layout");
         const cuuint64_t rest = (cuuint64_t)nbatch << (h - lo - M);
         dim[0] = 32;
         stride[2] = (E << C);  // bits C..lo-1
@@ -188,18 +188,21 @@ int encode_pass_map(CUtensorMap* m, const PassDesc& d, const float2* B, int h, i
         dim[3] = (cuuint64_t)1 << (lo - C);
         dim[4] = rest;
         box[0] = 32; box[3] = 1; box[4] = 1;
-        if (C == 4) {
-            dim[1] = 256; dim[2] = 2;
+        if (C <= 4) {  // 2^C entries per row (64 or 128 bytes), the window as 256 x 2^(M-8)
+            dim[0] = (cuuint64_t)2 << C; box[0] = (cuuint32_t)2 << C;
+            dim[1] = 256; dim[2] = (cuuint64_t)1 << (M - 8);
             stride[0] = E << lo; stride[1] = E << (lo + 8);
-            box[1] = 256; box[2] = 2;
+            box[1] = 256; box[2] = (cuuint32_t)1 << (M - 8);
         } else {
             dim[1] = (cuuint64_t)1 << (C - 4); dim[2] = (cuuint64_t)1 << M;
             stride[0] = 16 * E; stride[1] = E << lo;
             box[1] = (cuuint32_t)1 << (C - 4); box[2] = (cuuint32_t)1 << M;
         }
     }
+    // rows of 64 bytes (a 10-bit window above bit 0) take the 64-byte swizzle
+    const bool row64 = !is_bottom_pass(d.type) && TILE_BITS - d.M == 3;
     const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<float2*>(B), dim, stride, box, estr,
-                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, row64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS)
         return fail(TB_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ") for a pass of type " +

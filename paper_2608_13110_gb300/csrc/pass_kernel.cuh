@@ -66,13 +66,17 @@ __device__ __forceinline__ uint32_t pass_smem_u32(const void* p) {
 }
 
 // Tile bits (13) of a pass and where a consumer thread holds them.
-//   windows at address bit 0 (tile = the 13 lowest address bits, window
-//   bits 0..M-1, M <= 10): lanes hold tile bits 0..4, registers 5..9, the
-//   warp index 10..12;
-//   other windows (tile bits 0..C-1 = the C >= 4 lowest address bits, tile
-//   bits C..12 = the window): lane bits 0..4 hold tile bits 0, 4, 5, 6, 7,
-//   registers 8..12, the warp index 1..3.
-// Every window bit is a lane or register bit in both cases.
+//   LAY_BOT, windows at address bit 0 (tile = the 13 lowest address bits,
+//   window bits 0..M-1, M <= 10): lanes hold tile bits 0..4, registers
+//   5..9, the warp index 10..12;
+//   LAY_HIGH, other windows of M <= 9 bits (tile bits 0..C-1 = the C >= 4
+//   lowest address bits, tile bits C..12 = the window): lane bits 0..4 hold
+//   tile bits 0, 4, 5, 6, 7, registers 8..12, the warp index 1..3;
+//   LAY_LOW3, other windows of 10 bits (C = 3: tile bits 0..2 = the 3 lowest
+//   address bits, rows of 64 bytes): lanes hold tile bits 3..7, registers
+//   8..12, the warp index 0..2.
+// Every window bit is a lane or register bit in each case.
+constexpr int LAY_BOT = 0, LAY_HIGH = 1, LAY_LOW3 = 2;
 template <int TYPE_, int M_>
 struct Shape {
     static constexpr int TYPE = TYPE_;
@@ -83,10 +87,12 @@ struct Shape {
     static constexpr int BLK = pass_blk(TYPE, M);         // the turn's 4x4 block (-1: none)
     static constexpr int NB = 2 * NS + (XM >= 0 ? 2 : 0);  // coefficient blocks
     static constexpr int C = BOT ? 0 : TILE_BITS - M;  // tile bit of window bit 0
+    static constexpr int LAY = BOT ? LAY_BOT : (C == 3 ? LAY_LOW3 : LAY_HIGH);
     static constexpr int REG0 = BOT ? 5 : 8;            // tile bit of register bit 0
     static constexpr int regpos(int t) { return (t >= REG0 && t < REG0 + REG_BITS) ? t - REG0 : -1; }
     static constexpr int lanepos(int t) {
         if (BOT) return t < 5 ? t : -1;
+        if (LAY == LAY_LOW3) return (t >= 3 && t < 8) ? t - 3 : -1;
         return t == 0 ? 0 : (t >= 4 && t < 8) ? t - 3 : -1;
     }
     static constexpr int tgt(int i) { return C + step_spec(TYPE, M, i).t; }
@@ -108,10 +114,11 @@ struct Shape {
 };
 
 // Tile coordinate of a consumer thread's register entry 0.
-template <bool BOT>
+template <int LAY>
 __device__ __forceinline__ uint32_t thread_base(uint32_t tid) {
     const uint32_t lane = tid & 31u, warp = tid >> 5;
-    if (BOT) return lane | (warp << 10);
+    if (LAY == LAY_BOT) return lane | (warp << 10);
+    if (LAY == LAY_LOW3) return (lane << 3) | warp;
     return (lane & 1u) | ((lane >> 1) << 4) | (warp << 1);
 }
 
@@ -128,20 +135,29 @@ __device__ __forceinline__ uint32_t thread_base(uint32_t tid) {
 //   * windows at bit 0: tile bits 0..3, then 5..12, then 4. Lanes 0..3 hold
 //     tile bits 0..3 and registers bits 5..7, so the swizzled bits are
 //     t0, t1^t5, t2^t6, t3^t7: again a bijection of the lane bits.
+//   * 10-bit windows above bit 0 (LAY_LOW3): identity order in rows of 64
+//     bytes with the 64-byte swizzle (slot bits 1..2 ^= 4..5). Slot bit 0 is
+//     the warp's tile bit 0, so a half warp's 16 slots cover 8 bank pairs:
+//     two-way conflicts on these passes' stage reads and writes.
 // The map is linear over GF(2): for disjoint bit sets slot_of(a | b) =
 // slot_of(a) ^ slot_of(b), so a thread's 32 slots are its base slot XOR
 // compile-time constants.
 // ---------------------------------------------------------------------------
 __host__ __device__ constexpr uint32_t swz128(uint32_t s) { return s ^ (((s >> 4) & 7u) << 1); }
 
-template <bool BOT>
+// 64-byte swizzle (rows of 64 bytes, LAY_LOW3): slot bits 1..2 ^= 4..5.
+__host__ __device__ constexpr uint32_t swz64(uint32_t s) { return s ^ (((s >> 4) & 3u) << 1); }
+
+template <int LAY>
 __host__ __device__ constexpr uint32_t slot_of(uint32_t idx) {
+    if (LAY == LAY_LOW3) return swz64(idx);
+    constexpr bool BOT = LAY == LAY_BOT;
     return swz128(BOT ? ((idx & 15u) | (((idx >> 5) & 255u) << 4) | (((idx >> 4) & 1u) << 12)) : idx);
 }
 
-template <bool BOT, uint32_t J>
+template <int LAY, uint32_t J>
 struct SlotC {
-    static constexpr uint32_t v = slot_of<BOT>(J);
+    static constexpr uint32_t v = slot_of<LAY>(J);
 };
 
 // ---------------------------------------------------------------------------
@@ -412,23 +428,23 @@ __device__ __forceinline__ void stage_coefficients(const StepG* steps, float2* s
 
 // Registers <-> shared stage: entry j of a thread sits at tile coordinate
 // thread_base | j << REG0, i.e. slot base ^ SlotC<j << REG0>.
-template <bool BOT, int REG0, int J>
+template <int LAY, int REG0, int J>
 __device__ __forceinline__ void smem_read_j(float2 (&P)[16], float2 (&Q)[16], const float2* tile, uint32_t sb) {
     if constexpr (J < 32) {
-        const float2 e = tile[sb ^ SlotC<BOT, ((uint32_t)J << REG0)>::v];
+        const float2 e = tile[sb ^ SlotC<LAY, ((uint32_t)J << REG0)>::v];
         if constexpr (J < 16) { P[J].x = e.x; Q[J].x = e.y; }
         else                  { P[J - 16].y = e.x; Q[J - 16].y = e.y; }
-        smem_read_j<BOT, REG0, J + 1>(P, Q, tile, sb);
+        smem_read_j<LAY, REG0, J + 1>(P, Q, tile, sb);
     }
 }
 
-template <bool BOT, int REG0, int J>
+template <int LAY, int REG0, int J>
 __device__ __forceinline__ void smem_write_j(const float2 (&P)[16], const float2 (&Q)[16], float2* tile,
                                              uint32_t sb) {
     if constexpr (J < 32) {
-        tile[sb ^ SlotC<BOT, ((uint32_t)J << REG0)>::v] =
+        tile[sb ^ SlotC<LAY, ((uint32_t)J << REG0)>::v] =
             J < 16 ? make_float2(P[J & 15].x, Q[J & 15].x) : make_float2(P[J & 15].y, Q[J & 15].y);
-        smem_write_j<BOT, REG0, J + 1>(P, Q, tile, sb);
+        smem_write_j<LAY, REG0, J + 1>(P, Q, tile, sb);
     }
 }
 
@@ -681,7 +697,7 @@ __global__ void __launch_bounds__(PASS_THREADS, PASS_CTAS_PER_SM)
     float scale = 1.0f;
     uint32_t xmask = 0;
     const int64_t tmask = ((int64_t)1 << p.tile_shift) - 1;
-    const uint32_t sb = slot_of<SH::BOT>(thread_base<SH::BOT>(tid));
+    const uint32_t sb = slot_of<SH::LAY>(thread_base<SH::LAY>(tid));
     int s = 0;
     uint32_t ph = 0;
     for (int64_t k = 0; k < ntl; ++k) {
@@ -708,12 +724,12 @@ __global__ void __launch_bounds__(PASS_THREADS, PASS_CTAS_PER_SM)
 
         float2* tile = stages + s * TILE;
         float2 P[16], Q[16];
-        smem_read_j<SH::BOT, SH::REG0, 0>(P, Q, tile, sb);
+        smem_read_j<SH::LAY, SH::REG0, 0>(P, Q, tile, sb);
         run_steps<SH, 0>(P, Q, sc, xmask, scale, tid);
 #pragma unroll
         for (int j = 0; j < 16; ++j)
             runmax = fmaxf(runmax, fmaxf(fmaxf(fabsf(P[j].x), fabsf(P[j].y)), fmaxf(fabsf(Q[j].x), fabsf(Q[j].y))));
-        smem_write_j<SH::BOT, SH::REG0, 0>(P, Q, tile, sb);
+        smem_write_j<SH::LAY, SH::REG0, 0>(P, Q, tile, sb);
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // visible to the tensor store
         __syncwarp();
         if ((tid & 31u) == 0) pbar_arrive(done0 + 8 * s);

@@ -283,15 +283,19 @@ static void build_pass_steps(Plan& P) {
 }
 
 // Modelled time of a schedule in units of one HBM pass: a pass costs the
-// larger of its memory time and its arithmetic time (alpha per step). A
-// 10-bit window of a forward or reversed row whose address span reaches 2^27
-// entries (1 GiB: its tile touches about 512 pages of 2 MB) measured 5-24 %
-// slower than the same window lower in the address space; it costs gamma more.
+// larger of its memory time and its arithmetic time (alpha per step; a turn
+// block counts as two steps). A 10-bit window above address bit 0 moves its
+// tiles in rows of 64 bytes and measured about 1.35 passes (widths 32 and 35);
+// a 10-bit window of a forward or reversed row whose address span reaches 2^27
+// entries (1 GiB: its tile touches about 512 pages of 2 MB) costs gamma more.
 static double schedule_cost(const std::vector<PassDesc>& ps) {
-    const double alpha = 0.105, gamma = 0.25;
+    const double alpha = 0.105, gamma = 0.25, row64 = 0.35;
     double c = 0;
     for (const auto& p : ps) {
-        c += std::max(1.0, alpha * p.nsteps);
+        const int steps = p.nsteps + (pass_blk(p.type, p.M) >= 0 ? 1 : 0);
+        c += std::max(1.0, alpha * steps);
+        const bool high = p.type != P_BOT && p.type != P_BOT_START && p.type != P_BOT_END;
+        if (high && p.M == MAX_WINDOW_HIGH && TILE_BITS - p.M == 3) c += row64;
         if ((p.type == P_FWD || p.type == P_REV) && p.M >= 10 && p.lo + p.M >= 27) c += gamma;
     }
     return c;
@@ -605,7 +609,7 @@ int plan_build(Plan& P, int n, int d, const uint8_t* cliff, const uint8_t* tmask
             return TB_EINVAL;
         }
         if (t_lo < MIN_WINDOW || t_hi > MAX_WINDOW_HIGH) {
-            err = "top_bits must be in 5..9";
+            err = "top_bits must be in 5..10";
             return TB_EINVAL;
         }
         double best = 1e300;

@@ -19,7 +19,7 @@ constexpr int PASS_CTAS_PER_SM = 1;
 constexpr int REG_BITS = 5;           // entries per thread = 2^REG_BITS
 constexpr int MIN_WINDOW = 5;
 constexpr int MAX_WINDOW = 10;        // window at address bit 0 (whole tile is low bits)
-constexpr int MAX_WINDOW_HIGH = TILE_BITS - 4;  // other windows keep >= 16 consecutive entries (128 B)
+constexpr int MAX_WINDOW_HIGH = TILE_BITS - 3;  // other windows keep >= 8 consecutive entries (64 B)
 // Boundaries of width <= SMALL_H_MAX live in one CTA's shared memory for the
 // whole sweep (one CTA per bitstring).
 constexpr int SMALL_H_MAX = 12;

@@ -191,9 +191,7 @@ def test_pass_cases_cover_every_shape(tb):
     seen = set()
     for n, d, wb, bb, tt in mod.PASS_CASES:
         seen |= {(s, m) for s, m, _ in tb.Plan(n, d, window_bits=wb, bottom_bits=bb, top_bits=tt).schedule}
-    bottom = {"bot", "bot_start", "bot_end"}
-    assert seen == {(s, m) for s in tb.Plan.PASS_SHAPES if s != "tensor"
-                    for m in range(5, 11 if s in bottom else 10)}
+    assert seen == {(s, m) for s in tb.Plan.PASS_SHAPES if s != "tensor" for m in range(5, 11)}
 
 
 # ------------------------------------------------ split-precision tensor-core schedule

@@ -61,13 +61,14 @@ def test_narrow_random_unitaries(tb, oracle_mod, n, d):
 # ------------------------------------------------------- HBM pass schedule
 
 # (n, d, window_bits, bottom_bits, top_bits): together these schedules use
-# every pass shape with every window size it admits (5..10 at address bit 0,
-# 5..9 elsewhere; checked on the host in
+# every pass shape with every window size it admits (5..10; 10-bit windows
+# above bit 0 use rows of 64 bytes; checked on the host in
 # tests/test_abi_host.py::test_pass_cases_cover_every_shape).
 PASS_CASES = [
     (6, 42, 6, 8, 5), (6, 46, 8, 6, 5), (6, 36, 9, 5, 6),
     (6, 32, 5, 9, 8), (6, 36, 5, 10, 9), (7, 26, 5, 5, 9),
     (7, 26, 5, 6, 8), (7, 26, 5, 7, 7), (7, 26, 5, 8, 6), (7, 26, 5, 9, 5),
+    (6, 28, 10, 5, 10), (6, 36, 10, 5, 5), (7, 28, 10, 5, 10), (6, 26, 5, 7, 7),
     (16, 40, 0, 0, 0), (17, 44, 0, 0, 0),
 ]
 
@@ -81,7 +82,7 @@ def test_pass_schedule_vs_state_vector(tb, oracle_mod, n, d, wb, bb, tt):
     assert rel_l2(plan.amplitudes(c.bits), ref) < TOL
 
 
-@pytest.mark.parametrize("n,d,wb,bb,tt", PASS_CASES[:10])
+@pytest.mark.parametrize("n,d,wb,bb,tt", PASS_CASES[:13])
 def test_every_pass_shape_random_unitaries(tb, oracle_mod, n, d, wb, bb, tt):
     """Haar one-qubit gates on every slot: the turn passes' composed 4x4 blocks
     and every other step with dense, unstructured coefficients."""
