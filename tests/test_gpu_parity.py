@@ -251,3 +251,24 @@ def test_maximum_width_33_closed_form(tb, oracle_mod):
     assert plan.info["boundary_bits"] == 33
     ref = oracle_mod.closed_form_hdiag(c, bits)
     assert rel_l2(plan.amplitudes(bits), ref) < TOL
+
+
+def test_maximum_width_35_closed_form(tb, oracle_mod):
+    """The widest boundary the device path evaluates: n = d = 70, width 35
+    (2^35 complex64 = 256 GiB: the paper's largest intermediate) in one GPU's
+    HBM, windows 10 / bottom 10 / top 9 (10-bit windows above address bit 0
+    at full size), against the exact amplitude of an H / diagonal / H
+    circuit."""
+    import torch
+    c = W.hdiag_circuit(70, 70, 468, 0, 4350)
+    bits = _nonzero_bits(c, oracle_mod, 1, 9)
+    plan = tb.Plan.from_circuit(c, window_bits=10, bottom_bits=10, top_bits=9)
+    assert plan.info["boundary_bits"] == 35
+    torch.cuda.empty_cache()
+    if torch.cuda.mem_get_info()[0] < plan.workspace_bytes(1) + (2 << 30):
+        pytest.skip("the device has no room for a 2^35-entry boundary")
+    try:
+        got = plan.amplitudes(bits)
+    finally:
+        torch.cuda.empty_cache()
+    assert rel_l2(got, oracle_mod.closed_form_hdiag(c, bits)) < TOL
