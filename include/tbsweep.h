@@ -93,7 +93,10 @@ typedef struct {
                                split products hi.hi + hi.lo + lo.hi accumulated
                                in FP32 (window options are then ignored). */
     int64_t hbm_budget_bytes; /* cap on the boundary batch a call keeps on the
-                                 device (0 = no cap beyond the workspace) */
+                                 device (0 = no cap beyond the workspace); an
+                                 open plan whose budget cannot hold two
+                                 boundaries works in place (see
+                                 tb_plan_create_open) */
 } tb_opts;
 
 /* Plan summary. */
