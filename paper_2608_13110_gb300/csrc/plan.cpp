@@ -282,11 +282,13 @@ static void build_pass_steps(Plan& P) {
     }
 }
 
-// Modelled time of a schedule in units of one HBM pass: a pass costs the
-// larger of its memory time and its arithmetic time (alpha per step; a turn
-// block counts as two steps). A 10-bit window above address bit 0 moves its
-// tiles in rows of 64 bytes and measured about 1.35 passes (widths 32 and 35);
-// a 10-bit window of a forward or reversed row whose address span reaches 2^27
+// Modelled time of a schedule in units of one HBM pass, a heuristic for the
+// planner's default (the autotuner times candidates on the device): a pass
+// costs the larger of its memory time and its arithmetic time (alpha per
+// step; a turn block counts as two steps). A 10-bit window above address bit
+// 0 (tiles in rows of 64 bytes) is charged row64 more, which keeps the default
+// at width 32 on the schedule measured fastest there (windows 9 / 10 / 7); a
+// 10-bit window of a forward or reversed row whose address span reaches 2^27
 // entries (1 GiB: its tile touches about 512 pages of 2 MB) costs gamma more.
 static double schedule_cost(const std::vector<PassDesc>& ps) {
     const double alpha = 0.105, gamma = 0.25, row64 = 0.35;
