@@ -687,6 +687,7 @@ def run_open_workload(args, rank, world, local):
 # contraction), width 35 (a 256 GiB complex64 boundary), 32.16 s per
 # steady-state contraction on one node of 8 H100 GPUs.
 PAPER_S_PER_CONTRACTION = 32.16
+PAPER_FIRST_USE_S = 54.63  # first contraction of a job (handles, plan and workspace caches)
 PAPER_AMPS_PER_CONTRACTION = 256
 
 
@@ -708,6 +709,7 @@ def run_paper_workload(args, rank, world, local):
     # windows 10 / bottom 10 / top 9: the fastest of the schedules timed at width
     # 35 on a GB300 (8 absorbed rows: 3087 ms; 9 / 7 / 7: 3156 ms; the planner's
     # default 3217 ms); autotuning inside the run would time 256 GiB sweeps
+    t_first = time.perf_counter()  # first use: plan, workspace, upload and the first contraction
     plan = tb.Plan.from_circuit(c, open_k=k, window_bits=10, bottom_bits=10, top_bits=9)
     info = plan.info
     need = plan.workspace_bytes(1)
@@ -722,8 +724,12 @@ def run_paper_workload(args, rank, world, local):
     plan.upload(ws, stream)
     d_pre = torch.from_numpy(prefixes).to(dev)
     d_out = torch.empty((na << k, 2), dtype=torch.float64, device=dev)
-    for _ in range(args.warmup):
-        plan.amplitudes_device(d_pre, ws, d_out, stream)
+    first_use = None
+    for w in range(args.warmup):
+        plan.amplitudes_device(d_pre[:1] if w == 0 else d_pre, ws, d_out, stream)
+        if w == 0:
+            torch.cuda.synchronize(dev)
+            first_use = time.perf_counter() - t_first
     torch.cuda.synchronize(dev)
     barrier(world, dev)
     clocks = ClockSampler(local)
@@ -760,7 +766,9 @@ def run_paper_workload(args, rank, world, local):
                        "schedule": {"given": {"window_bits": 10, "bottom_bits": 10, "top_bits": 9}},
                        "pass_arithmetic": "fp32", "parallelism": f"replicas x{world}"},
             "s_per_contraction": t / (na * args.steps),
+            "first_use_s": first_use,  # plan + 260 GiB workspace + upload + first contraction (wall clock)
             "baseline": {"s_per_contraction": PAPER_S_PER_CONTRACTION, "amps_per_s": paper_rate,
+                         "first_use_s": PAPER_FIRST_USE_S,
                          "hardware": "one node of 8 NVIDIA H100 GPUs (cuTENSORMp, MPI)",
                          "source": "the paper's table of full-depth results (Sec. 5.2)"},
             "e2e": {"value": world * na * (1 << k) / t_e2e, "unit": UNIT,
