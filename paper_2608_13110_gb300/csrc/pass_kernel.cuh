@@ -7,12 +7,15 @@
 //
 // A pass applies a compile-time sequence of controlled 2x2 steps to every
 // tile of 2^13 complex64 entries: the window's M address bits plus 13-M low
-// address bits (the 13 lowest bits when the window starts at bit 0).
+// address bits (the 13 lowest bits when the window starts at bit 0). At a row
+// turn the four steps on the window's two outermost bits run as one 4x4 block
+// (composed on the host, see tb_internal.h).
 //
 // Warp-specialised, one persistent CTA per SM:
 //   * one producer thread moves whole tiles between HBM and a 3-stage ring of
 //     shared-memory stages with tensor copies (cp.async.bulk.tensor, 128-byte
-//     swizzle): a load completes on the stage's "full" mbarrier; once the
+//     swizzle; 64-byte rows and swizzle for 10-bit windows above bit 0): a
+//     load completes on the stage's "full" mbarrier; once the
 //     consumers have written the stage back it is stored in place with one
 //     bulk tensor store, and as soon as the store has read the stage the next
 //     tile's load is issued into it;
@@ -26,7 +29,8 @@
 //     and arrives on the stage's "done" mbarrier. HBM traffic, shared-memory
 //     traffic and the arithmetic of different warps all overlap.
 // The tensor map orders the tile's address bits so that every warp access to
-// a stage is free of shared-memory bank conflicts (see slot_of).
+// a stage is free of shared-memory bank conflicts, except in the 64-byte-row
+// layout, where they are two-way (see slot_of).
 //
 // Rescaling: the producer of this pass's input left max(|re|,|im|) of its
 // output in maxs[slot]; this pass multiplies its input by 2^s (exact; folded
